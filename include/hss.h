@@ -1,0 +1,156 @@
+/*
+ * hss.h -- C ABI of the GB300 HSS-ULV factorization and solve.
+ *
+ * The library factors a symmetric positive definite HSS (hierarchically
+ * semiseparable) matrix with the ULV algorithm of Sec. 3 of "O(N) distributed
+ * direct factorization of structured dense matrices using runtime systems"
+ * (Alg. 2), solves with the factor (the solve formula of Sec. 3.2) and returns
+ * the log-determinant.  Everything runs on one CUDA device in hand-written
+ * kernels; there is no CPU fallback.
+ *
+ * Matrix format (Sec. 2, HSS construction and Eq. hss-block-notation), for a
+ * uniform binary tree with leaves at level L and the root at level 0:
+ *   - node i of level l has children 2i and 2i+1 of level l+1;
+ *   - leaf diagonal blocks D_i (leaf x leaf), i = 0 .. 2^L - 1;
+ *   - leaf bases U_i (leaf x rank);
+ *   - transfer matrices E_{l;i} (2 rank x rank), levels l = 1 .. L-1, giving the
+ *     nested basis Ũ_{l;i} = blkdiag(Ũ_{l+1;2i}, Ũ_{l+1;2i+1}) E_{l;i};
+ *   - couplings S_{l;k} (rank x rank), levels l = 1 .. L, between siblings
+ *     2k and 2k+1 of level l:  A(I_{2k+1}, I_{2k}) = Ũ_{2k+1} S_{l;k} Ũ_{2k}ᵀ
+ *     (and its transpose above the diagonal).
+ * All blocks are column-major FP64, packed without gaps:
+ *   D: 2^L blocks of leaf*leaf, U: 2^L blocks of leaf*rank,
+ *   E: level 1 first, then 2, ... L-1; level l holds 2^l blocks of 2rank*rank,
+ *   S: level 1 first, then 2, ... L;   level l holds 2^(l-1) blocks of rank*rank.
+ * The bases need full column rank; they need not be orthonormal.
+ * Vectors are in cluster (tree) order: rows i*leaf .. (i+1)*leaf-1 belong to
+ * leaf i.  Multi-column vectors are column-major with leading dimension ld.
+ *
+ * Streams: every call that takes `stream` (a cudaStream_t, NULL = legacy
+ * default stream) is asynchronous on it unless stated.  Errors detected on the
+ * device (a non-positive pivot) surface at the next synchronizing call:
+ * hss_logdet, hss_last_info, hss_sync, or hss_solve of a mixed-precision factor.
+ *
+ * Return codes: HSS_OK (0) or a negative HSS_ERR_* code; hss_strerror names it.
+ */
+#ifndef HSS_GB300_H
+#define HSS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HSS_OK 0
+#define HSS_ERR_INVALID_ARG (-1)   /* bad pointer, size or option */
+#define HSS_ERR_NOT_FACTORIZED (-2) /* solve / logdet before a successful factorize */
+#define HSS_ERR_NOT_SPD (-3)        /* a Cholesky pivot was not positive (see hss_last_info) */
+#define HSS_ERR_CUDA (-4)           /* a CUDA runtime call or kernel launch failed */
+#define HSS_ERR_OOM (-5)            /* device allocation failed */
+#define HSS_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
+#define HSS_ERR_NO_CONVERGENCE (-7) /* iterative refinement hit its iteration limit */
+
+typedef struct hss_s* hss_t;
+
+/* Arithmetic of the factorization.  HSS_FP64 computes every step in FP64.
+ * The mixed modes compute the per-level steps (Alg. 2 lines 2-4) in lower
+ * precision and use the factor as the preconditioner of FP64 iterative
+ * refinement in hss_solve; the root Cholesky, residual and update are FP64. */
+typedef enum {
+  HSS_FP64 = 0,
+  HSS_MIXED_TF32 = 1,
+  HSS_MIXED_BF16 = 2,
+  HSS_MIXED_FP32 = 3
+} hss_precision;
+
+typedef struct {
+  int32_t n;      /* matrix order, = leaf * 2^levels */
+  int32_t leaf;   /* leaf block order (1 .. 768) */
+  int32_t rank;   /* rank of every basis (1 .. min(leaf, 256)) */
+  int32_t levels; /* L >= 1 */
+} hss_shape;
+
+typedef struct {
+  int32_t precision; /* hss_precision */
+  int32_t ir_max_it; /* refinement iteration limit (mixed modes), e.g. 30 */
+  double ir_tol;     /* stop when every column has ‖b - A x‖₂ / ‖b‖₂ <= ir_tol */
+} hss_options;
+
+/* Create a device-resident HSS object from its generators (format above).
+ * D, U, E, S are host pointers (on_device = 0) or device pointers of the current
+ * device (on_device = 1); they are copied and the caller keeps ownership.  The
+ * object owns one device arena (inputs, factor, workspace for up to 32
+ * right-hand-side columns per pass); it is tied to the device current at
+ * creation.  E may be NULL when levels = 1.  Synchronous (returns after the
+ * copies).  Errors: INVALID_ARG (sizes out of range, NULL pointers), OOM, CUDA. */
+int hss_create(const hss_shape* shape, const double* D, const double* U, const double* E,
+               const double* S, int on_device, hss_t* out);
+
+/* ULV factorization, Alg. 2: for l = L .. 1, for every node of level l,
+ * (a) complete the node basis to an orthogonal Q = [Q^R Q^S] (Householder QL,
+ *     Eq. 2-3), (b) form Qᵀ A_i Q (diagonal product, Eq. dense-split),
+ * (c) partial Cholesky of the redundant block with the TRSM and SYRK of Eq.
+ *     partial-Cholesky, and (d) merge sibling Schur complements and the
+ *     rescaled coupling into the parent's 2rank x 2rank block; then the root
+ *     Cholesky.  The factor replaces any previous one.  opt may be NULL (FP64).
+ * Asynchronous; a non-positive pivot is reported by the next synchronizing
+ * call as HSS_ERR_NOT_SPD with its level, node and column. */
+int hss_factorize(hss_t h, const hss_options* opt, void* stream);
+
+/* Solve A x = b with the factor (Sec. 3.2): forward sweep leaves -> root
+ * (apply Qᵀ, L^RR⁻¹, update and push the skeleton part to the parent), root
+ * Cholesky solve, backward sweep root -> leaves.  b and x are device pointers,
+ * n x nrhs column-major with leading dimension ld >= n; x may equal b.  With an
+ * FP64 factor the call is asynchronous.  With a mixed factor it runs FP64
+ * iterative refinement (residual by the HSS matvec) and synchronizes once per
+ * iteration; it returns HSS_ERR_NO_CONVERGENCE if ir_max_it is reached (x then
+ * holds the last iterate).  Errors: NOT_FACTORIZED, INVALID_ARG, CUDA. */
+int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, void* stream);
+
+/* log det A from the factorized form (Eq. hss-ulv-final-form): twice the sum of
+ * the logs of the diagonals of every L^RR and of the root factor.  Writes one
+ * host double.  Synchronizes the object's last stream.  Errors: NOT_FACTORIZED,
+ * NOT_SPD. */
+int hss_logdet(hss_t h, double* out);
+
+/* y = A x with the HSS generators (the product A·b of the construction-error
+ * formula in Sec. 5.1): upward pass through U and E, sibling couplings, downward
+ * pass, leaf blocks.  FP64.  x and y are device pointers (n x nrhs, ld), must
+ * not overlap.  Asynchronous.  Needs no factorization. */
+int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, void* stream);
+
+/* Block until the object's work is done and report any device-side failure
+ * (HSS_ERR_NOT_SPD ...). */
+int hss_sync(hss_t h);
+
+/* Details of the last factorization / solve (any pointer may be NULL): the
+ * level, node and column of a failed pivot (-1 if none), and the refinement
+ * iteration count and final max relative residual of the last mixed solve.
+ * Synchronizes.  Returns the pending device error code, if any. */
+int hss_last_info(hss_t h, int32_t* level, int32_t* node, int32_t* col, int32_t* ir_iters,
+                  double* ir_resid);
+
+/* Copy one per-level array of the factor to host memory, for inspection and
+ * per-step tests.  what: 0 = V (Householder vectors, b x rank per node, unit
+ * diagonal explicit), 1 = T (compact-WY factor, rank x rank upper; Q = I - V T Vᵀ),
+ * 2 = L_B (rank x rank lower, L_B = Q^Sᵀ B), 3 = factored block (b x b: lower
+ * triangle holds L^RR, L^SR and the Schur complement Â^SS), 4 = basis fed to
+ * the basis completion of level l < L (2 rank x rank per node: the merge output
+ * blkdiag(L_B(2i), L_B(2i+1)) E_{l;i}).
+ * dst receives 2^l blocks back to back; count is its capacity in doubles.
+ * Synchronizes.  Errors: INVALID_ARG, NOT_FACTORIZED, and INVALID_ARG when the
+ * factor is not FP64. */
+int hss_export(hss_t h, int32_t what, int32_t level, double* dst, size_t count);
+
+/* Free the object and its device memory. NULL is ignored. */
+void hss_destroy(hss_t h);
+
+/* Static string naming a return code. */
+const char* hss_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSS_GB300_H */

@@ -135,6 +135,26 @@ class ULVFactor:
         self.dtype = np.float64
 
 
+def node_step(A, B, dtype=np.float64, level=-1, node=-1):
+    """One node of Alg. 2: basis completion (Eq. 2-3), diagonal product
+    Â = Qᵀ A Q (line 2) and partial Cholesky (line 3, Eq. partial-Cholesky).
+    Returns (Q, L_B, Â, L^RR, L^SR, Â^SS)."""
+    A = np.asarray(A, dtype=dtype)
+    B = np.asarray(B, dtype=dtype)
+    b, r = B.shape
+    c = b - r
+    Q, LB = complete_basis(B, dtype)
+    Ah = Q.T @ A @ Q
+    Ah = 0.5 * (Ah + Ah.T)
+    LRR = _chol(Ah[:c, :c], level, node) if c > 0 else np.zeros((0, 0), dtype)
+    if c > 0:
+        LSR = sla.solve_triangular(LRR, Ah[c:, :c].T, lower=True).T
+    else:
+        LSR = np.zeros((r, 0), dtype)
+    SS = Ah[c:, c:] - LSR @ LSR.T
+    return Q, LB, Ah, LRR, LSR, SS
+
+
 def factor(h, dtype=np.float64) -> ULVFactor:
     """Alg. 2: for l = L..1 {diagonal product; partial Cholesky; merge}; Cholesky(A_0).
 
@@ -152,17 +172,7 @@ def factor(h, dtype=np.float64) -> ULVFactor:
             getattr(F, key)[l] = []
         for i in range(2 ** l):
             A, B = A_lvl[i], B_lvl[i]
-            b, r = B.shape
-            c = b - r
-            Q, LB = complete_basis(B, dtype)                 # Eq. 2-3
-            Ah = Q.T @ A @ Q                                 # Alg. 2 line 2
-            Ah = 0.5 * (Ah + Ah.T)
-            LRR = _chol(Ah[:c, :c], l, i) if c > 0 else np.zeros((0, 0), dtype)
-            if c > 0:                                        # Eq. partial-Cholesky
-                LSR = sla.solve_triangular(LRR, Ah[c:, :c].T, lower=True).T
-            else:
-                LSR = np.zeros((r, 0), dtype)
-            SS = Ah[c:, c:] - LSR @ LSR.T
+            Q, LB, Ah, LRR, LSR, SS = node_step(A, B, dtype, l, i)
             F.Q[l].append(Q); F.LB[l].append(LB); F.LRR[l].append(LRR)
             F.LSR[l].append(LSR); F.SS[l].append(SS); F.Ahat[l].append(Ah)
             F.Anode[l].append(A); F.Bnode[l].append(B)

@@ -1,0 +1,291 @@
+// Batched SIMT GEMM / SYR2K for the FP64 (and FP32) ULV path.
+//
+// On GB300 the FP64 pipe retires about 2 DFMA per clock per SM, so these
+// kernels are bound by DFMA issue, not by memory: a 64x64 output tile with a
+// 4x4 register micro-tile per thread keeps 16 independent DFMAs in flight per
+// thread against 8 shared-memory loads, and the only other goal is enough
+// CTAs to cover all 152 SMs.  Tall-skinny products (n <= 32 columns, the
+// right-hand-side blocks of the solve and matvec) use a separate kernel whose
+// warps own whole columns, so that no warp issues DFMAs on padding.
+#include "common.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <typename T, bool TA, bool TB, bool BETA>
+__global__ void __launch_bounds__(NT)
+gemm_tile_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, long long sA,
+                 const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
+                 long long sC) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const long long bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+
+  for (int k0 = 0; k0 < k; k0 += BK) {
+#pragma unroll
+    for (int e0 = 0; e0 < BM * BK; e0 += NT) {
+      const int e = e0 + threadIdx.x;
+      int i, kk;
+      if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
+      const int gi = i0 + i, gk = k0 + kk;
+      T v = T(0);
+      if (gi < m && gk < k) v = TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
+      As[kk][i] = v;
+    }
+#pragma unroll
+    for (int e0 = 0; e0 < BN * BK; e0 += NT) {
+      const int e = e0 + threadIdx.x;
+      int j, kk;
+      if (!TB) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+      const int gj = j0 + j, gk = k0 + kk;
+      T v = T(0);
+      if (gj < n && gk < k) v = TB ? B[gj + (long long)gk * ldb] : B[gk + (long long)gj * ldb];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        a[t] = As[kk][tx + 16 * t];
+        b[t] = Bs[kk][ty + 16 * t];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gj = j0 + ty + 16 * q;
+    if (gj >= n) continue;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int gi = i0 + tx + 16 * p;
+      if (gi >= m) continue;
+      T* c = C + gi + (long long)gj * ldc;
+      *c = BETA ? fma(alpha, acc[p][q], beta * *c) : alpha * acc[p][q];
+    }
+  }
+}
+
+// tall-skinny: C (m x n, n <= 32) ; CTA = 64 rows x all n columns.
+// warp w owns columns w, w + 8, w + 16, w + 24; lane owns rows lane, lane + 32.
+template <typename T, bool TA, bool TB, bool BETA>
+__global__ void __launch_bounds__(NT)
+gemm_skinny_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, long long sA,
+                   const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
+                   long long sC) {
+  constexpr int SBK = 32;
+  __shared__ T As[SBK][BM + 1];
+  __shared__ T Bs[32][SBK + 1];   // Bs[j][kk]
+  const long long bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int i0 = blockIdx.x * BM;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = T(0);
+  for (int k0 = 0; k0 < k; k0 += SBK) {
+    for (int e = threadIdx.x; e < BM * SBK; e += NT) {
+      int i, kk;
+      if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % SBK; i = e / SBK; }
+      const int gi = i0 + i, gk = k0 + kk;
+      T v = T(0);
+      if (gi < m && gk < k) v = TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
+      As[kk][i] = v;
+    }
+    for (int e = threadIdx.x; e < 32 * SBK; e += NT) {
+      int j, kk;
+      if (!TB) { kk = e % SBK; j = e / SBK; } else { j = e % 32; kk = e / 32; }
+      const int gk = k0 + kk;
+      T v = T(0);
+      if (j < n && gk < k) v = TB ? B[j + (long long)gk * ldb] : B[gk + (long long)j * ldb];
+      Bs[j][kk] = v;
+    }
+    __syncthreads();
+    if (w < n) {
+#pragma unroll 4
+      for (int kk = 0; kk < SBK; ++kk) {
+        const T a0 = As[kk][lane], a1 = As[kk][lane + 32];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = w + 8 * q;   // warp-uniform
+          if (j < n) {
+            const T bv = Bs[j][kk];
+            acc[q][0] = fma(a0, bv, acc[q][0]);
+            acc[q][1] = fma(a1, bv, acc[q][1]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = w + 8 * q;
+    if (j >= n) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gi = i0 + lane + 32 * h;
+      if (gi >= m) continue;
+      T* c = C + gi + (long long)j * ldc;
+      *c = BETA ? fma(alpha, acc[q][h], beta * *c) : alpha * acc[q][h];
+    }
+  }
+}
+
+template <typename T, bool TA, bool TB>
+void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA, const T* B,
+                 int ldb, long long sB, T beta, T* C, int ldc, long long sC, int batch,
+                 cudaStream_t st) {
+  const bool useb = beta != T(0);
+  if (n <= 32) {
+    dim3 g((m + BM - 1) / BM, 1, batch);
+    if (useb)
+      gemm_skinny_kernel<T, TA, TB, true><<<g, NT, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
+                                                           beta, C, ldc, sC);
+    else
+      gemm_skinny_kernel<T, TA, TB, false><<<g, NT, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb,
+                                                            sB, beta, C, ldc, sC);
+    return;
+  }
+  dim3 g((m + BM - 1) / BM, (n + BN - 1) / BN, batch);
+  if (useb)
+    gemm_tile_kernel<T, TA, TB, true><<<g, NT, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
+                                                       beta, C, ldc, sC);
+  else
+    gemm_tile_kernel<T, TA, TB, false><<<g, NT, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
+                                                        beta, C, ldc, sC);
+}
+
+// lower-triangle tiles only: blockIdx.x enumerates tile pairs (ti >= tj)
+template <typename T>
+__global__ void __launch_bounds__(NT)
+syr2k_lower_kernel(int m, int k, const T* A, int lda, long long sA, const T* __restrict__ P,
+                   int ldp, long long sP, const T* __restrict__ Q, int ldq, long long sQ, T* M,
+                   int ldm, long long sM) {
+  __shared__ T Pi[BK][BM + 1], Qi[BK][BM + 1], Pj[BK][BN + 1], Qj[BK][BN + 1];
+  const long long bz = blockIdx.y;
+  A += bz * sA;
+  P += bz * sP;
+  Q += bz * sQ;
+  M += bz * sM;
+  // decode tile pair
+  int t = blockIdx.x, ti = 0;
+  while (t > ti) { t -= ti + 1; ++ti; }
+  const int tj = t;
+  const int i0 = ti * BM, j0 = tj * BN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int k0 = 0; k0 < k; k0 += BK) {
+#pragma unroll
+    for (int e0 = 0; e0 < BM * BK; e0 += NT) {
+      const int e = e0 + threadIdx.x;
+      const int i = e % BM, kk = e / BM;
+      const int gk = k0 + kk;
+      const int gi = i0 + i, gj = j0 + i;
+      const bool okk = gk < k;
+      Pi[kk][i] = (okk && gi < m) ? P[gi + (long long)gk * ldp] : T(0);
+      Qi[kk][i] = (okk && gi < m) ? Q[gi + (long long)gk * ldq] : T(0);
+      Pj[kk][i] = (okk && gj < m) ? P[gj + (long long)gk * ldp] : T(0);
+      Qj[kk][i] = (okk && gj < m) ? Q[gj + (long long)gk * ldq] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T pa[4], qa[4], pb[4], qb[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        pa[s] = Pi[kk][tx + 16 * s];
+        qa[s] = Qi[kk][tx + 16 * s];
+        pb[s] = Pj[kk][ty + 16 * s];
+        qb[s] = Qj[kk][ty + 16 * s];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[p][q] = fma(pa[p], qb[q], acc[p][q]);
+          acc[p][q] = fma(qa[p], pb[q], acc[p][q]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gj = j0 + ty + 16 * q;
+    if (gj >= m) continue;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int gi = i0 + tx + 16 * p;
+      if (gi >= m || gi < gj) continue;
+      M[gi + (long long)gj * ldm] = A[gi + (long long)gj * lda] - acc[p][q];
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void gemm_batched(bool transA, bool transB, int m, int n, int k, T alpha, const T* A, int lda,
+                  long long sA, const T* B, int ldb, long long sB, T beta, T* C, int ldc,
+                  long long sC, int batch, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || batch <= 0) return;
+  if (k <= 0) {
+    // C = beta * C: express as a GEMM with a zero operand of depth 1 is not
+    // possible without a buffer; callers never pass k = 0 with beta != 1.
+    return;
+  }
+  if (!transA && !transB)
+    launch_gemm<T, false, false>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, st);
+  else if (transA && !transB)
+    launch_gemm<T, true, false>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, st);
+  else if (!transA && transB)
+    launch_gemm<T, false, true>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, st);
+  else
+    launch_gemm<T, true, true>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, st);
+}
+
+template <typename T>
+void syr2k_lower_batched(int m, int k, const T* A, int lda, long long sA, const T* P, int ldp,
+                         long long sP, const T* Q, int ldq, long long sQ, T* M, int ldm,
+                         long long sM, int batch, cudaStream_t st) {
+  if (m <= 0 || batch <= 0) return;
+  const int nt = (m + BM - 1) / BM;
+  dim3 g(nt * (nt + 1) / 2, batch);
+  syr2k_lower_kernel<T><<<g, NT, 0, st>>>(m, k, A, lda, sA, P, ldp, sP, Q, ldq, sQ, M, ldm, sM);
+}
+
+template void gemm_batched<double>(bool, bool, int, int, int, double, const double*, int, long long,
+                                   const double*, int, long long, double, double*, int, long long,
+                                   int, cudaStream_t);
+template void gemm_batched<float>(bool, bool, int, int, int, float, const float*, int, long long,
+                                  const float*, int, long long, float, float*, int, long long, int,
+                                  cudaStream_t);
+template void syr2k_lower_batched<double>(int, int, const double*, int, long long, const double*,
+                                          int, long long, const double*, int, long long, double*,
+                                          int, long long, int, cudaStream_t);
+template void syr2k_lower_batched<float>(int, int, const float*, int, long long, const float*, int,
+                                         long long, const float*, int, long long, float*, int,
+                                         long long, int, cudaStream_t);

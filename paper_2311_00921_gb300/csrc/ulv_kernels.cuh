@@ -1,0 +1,26 @@
+// Launchers of the per-node ULV step kernels (ulv_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+template <typename T>
+void launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
+                     long long sT, T* LB, long long sL, int b, int r, int nodes, cudaStream_t st);
+
+template <typename T>
+size_t pchol_smem(int b);
+
+template <typename T>
+void launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int ldpa, long long sPA,
+                  double* logdet_part, int level, int node0, int* status, int nodes,
+                  cudaStream_t st);
+
+template <typename T>
+void launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
+                     int nrhs, T* Par, int ldpar, long long sPar, int nodes, cudaStream_t st);
+
+template <typename T>
+void launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
+                     int nrhs, const T* Par, int ldpar, long long sPar, int nodes,
+                     cudaStream_t st);
+
+void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t st);

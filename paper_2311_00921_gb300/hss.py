@@ -1,0 +1,207 @@
+"""Python binding of the C ABI in include/hss.h (ctypes; argument marshalling only).
+
+Device memory, streams and vectors are PyTorch tensors; every step of the
+factorization, solve and matvec runs in the CUDA library.  There is no CPU
+fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libhss_gb300.so")
+
+HSS_FP64, HSS_MIXED_TF32, HSS_MIXED_BF16, HSS_MIXED_FP32 = 0, 1, 2, 3
+PRECISIONS = {"fp64": HSS_FP64, "tf32": HSS_MIXED_TF32, "bf16": HSS_MIXED_BF16,
+              "fp32": HSS_MIXED_FP32}
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOT_FACTORIZED", -3: "NOT_SPD", -4: "CUDA",
+          -5: "OOM", -6: "TIMEOUT", -7: "NO_CONVERGENCE"}
+
+# every entry point declared in include/hss.h: name -> (restype, argtypes)
+_c_int, _c_double, _p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("leaf", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("levels", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("ir_max_it", ctypes.c_int32),
+                ("ir_tol", ctypes.c_double)]
+
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+SIGNATURES = {
+    "hss_create": (_c_int, [ctypes.POINTER(Shape), _p, _p, _p, _p, _c_int, ctypes.POINTER(_p)]),
+    "hss_factorize": (_c_int, [_p, ctypes.POINTER(Options), _p]),
+    "hss_solve": (_c_int, [_p, _p, _p, ctypes.c_int32, ctypes.c_int32, _p]),
+    "hss_logdet": (_c_int, [_p, ctypes.POINTER(_c_double)]),
+    "hss_matvec": (_c_int, [_p, _p, _p, ctypes.c_int32, ctypes.c_int32, _p]),
+    "hss_sync": (_c_int, [_p]),
+    "hss_last_info": (_c_int, [_p, _i32p, _i32p, _i32p, _i32p, ctypes.POINTER(_c_double)]),
+    "hss_export": (_c_int, [_p, ctypes.c_int32, ctypes.c_int32, _p, ctypes.c_size_t]),
+    "hss_destroy": (None, [_p]),
+    "hss_strerror": (ctypes.c_char_p, [_c_int]),
+}
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"HSS CUDA library not built ({LIB_PATH}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class HSSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({load().hss_strerror(code).decode()})")
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise HSSError(code, where)
+
+
+def _colmajor_blocks(blocks) -> np.ndarray:
+    """Stack 2-D blocks into one buffer with each block column-major."""
+    arr = np.stack([np.asarray(b, dtype=np.float64) for b in blocks])
+    return np.ascontiguousarray(arr.transpose(0, 2, 1))
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _mat_args(t):
+    """(pointer, nrhs, ld) of an n x nrhs column-major float64 CUDA tensor or a vector."""
+    import torch
+    if t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError("expected a float64 CUDA tensor")
+    if t.dim() == 1:
+        if t.stride(0) != 1:
+            raise ValueError("vector must be contiguous")
+        return t.data_ptr(), 1, t.shape[0]
+    if t.dim() != 2 or t.stride(0) != 1:
+        raise ValueError("matrix must be column-major (stride(0) == 1); use colmajor()")
+    return t.data_ptr(), t.shape[1], max(t.stride(1), t.shape[0])
+
+
+def colmajor(x, device="cuda"):
+    """A column-major float64 CUDA copy of a host array / tensor (n x k or n)."""
+    import torch
+    t = torch.as_tensor(np.asarray(x) if not isinstance(x, torch.Tensor) else x)
+    t = t.to(dtype=torch.float64)
+    if t.dim() == 1:
+        return t.contiguous().to(device)
+    return t.t().contiguous().to(device).t()
+
+
+class HSS:
+    """A device-resident HSS matrix (generators copied at construction)."""
+
+    def __init__(self, h):
+        if not h.uniform:
+            raise ValueError("the CUDA library takes uniform trees")
+        lib = load()
+        L, r, leaf = h.levels, h.rank, h.leaf
+        self.n, self.levels, self.rank, self.leaf = h.n, L, r, leaf
+        D = _colmajor_blocks(h.D)
+        U = _colmajor_blocks(h.U)
+        E = (np.concatenate([_colmajor_blocks(h.E[l]).ravel() for l in range(1, L)])
+             if L >= 2 else np.zeros(1))
+        S = np.concatenate([_colmajor_blocks(h.S[l]).ravel() for l in range(1, L + 1)])
+        shape = Shape(h.n, leaf, r, L)
+        out = _p()
+        _check(lib.hss_create(ctypes.byref(shape), D.ctypes.data, U.ctypes.data, E.ctypes.data,
+                              S.ctypes.data, 0, ctypes.byref(out)), "hss_create")
+        self._h = out
+        self.precision = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hss_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, stream=None):
+        opt = Options(PRECISIONS[precision], ir_max_it, ir_tol)
+        _check(load().hss_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
+               "hss_factorize")
+        self.precision = precision
+
+    def solve(self, b, x=None, stream=None):
+        """x = A⁻¹ b for column-major float64 CUDA tensors (x defaults to a new tensor)."""
+        import torch
+        if x is None:
+            x = torch.empty_like(b) if b.dim() == 1 else torch.empty(
+                (b.shape[1], b.shape[0]), dtype=b.dtype, device=b.device).t()
+        bp, nrhs, ld = _mat_args(b)
+        xp, nrhs2, ld2 = _mat_args(x)
+        if nrhs != nrhs2 or ld != ld2:
+            raise ValueError("b and x need the same shape and leading dimension")
+        _check(load().hss_solve(self._h, bp, xp, nrhs, ld, _stream_ptr(stream)), "hss_solve")
+        return x
+
+    def matvec(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x) if x.dim() == 1 else torch.empty(
+                (x.shape[1], x.shape[0]), dtype=x.dtype, device=x.device).t()
+        xp, nrhs, ld = _mat_args(x)
+        yp, nrhs2, ld2 = _mat_args(y)
+        if nrhs != nrhs2 or ld != ld2:
+            raise ValueError("x and y need the same shape and leading dimension")
+        _check(load().hss_matvec(self._h, xp, yp, nrhs, ld, _stream_ptr(stream)), "hss_matvec")
+        return y
+
+    def logdet(self) -> float:
+        out = ctypes.c_double()
+        _check(load().hss_logdet(self._h, ctypes.byref(out)), "hss_logdet")
+        return out.value
+
+    def sync(self):
+        _check(load().hss_sync(self._h), "hss_sync")
+
+    def last_info(self):
+        lvl, node, col, it = (ctypes.c_int32() for _ in range(4))
+        res = ctypes.c_double()
+        code = load().hss_last_info(self._h, ctypes.byref(lvl), ctypes.byref(node),
+                                    ctypes.byref(col), ctypes.byref(it), ctypes.byref(res))
+        return {"code": code, "level": lvl.value, "node": node.value, "col": col.value,
+                "ir_iters": it.value, "ir_resid": res.value}
+
+    def export(self, what: str, level: int) -> np.ndarray:
+        """Per-level factor arrays as (nodes, rows, cols) host arrays."""
+        kinds = {"V": 0, "T": 1, "LB": 2, "M": 3, "B": 4}
+        nodes = 2 ** level
+        b = self.leaf if level == self.levels else 2 * self.rank
+        r = self.rank
+        rows, cols = {"V": (b, r), "T": (r, r), "LB": (r, r), "M": (b, b), "B": (b, r)}[what]
+        buf = np.empty(nodes * rows * cols)
+        _check(load().hss_export(self._h, kinds[what], level, buf.ctypes.data, buf.size),
+               "hss_export")
+        return buf.reshape(nodes, cols, rows).transpose(0, 2, 1).copy()

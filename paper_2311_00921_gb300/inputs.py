@@ -188,18 +188,23 @@ class HSSMatrix:
 
 
 def _parallel_map(fn, items):
-    """Run fn over items on a thread pool (NumPy releases the GIL in its
-    element-wise kernels and BLAS calls, so row blocks evaluate in parallel)."""
+    """Run fn over items on a thread pool.  NumPy / LAPACK release the GIL; the
+    BLAS is limited to one thread per call inside the pool when threadpoolctl is
+    available, so the pool, not the BLAS, supplies the parallelism."""
     items = list(items)
     if len(items) <= 1:
-        for it in items:
-            fn(it)
-        return
+        return [fn(it) for it in items]
     import concurrent.futures as cf
+    import contextlib
     import os
+    try:
+        from threadpoolctl import threadpool_limits
+        ctx = threadpool_limits(1)
+    except Exception:  # pragma: no cover - not installed everywhere
+        ctx = contextlib.nullcontext()
     workers = min(len(items), os.cpu_count() or 1)
-    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        list(ex.map(fn, items))
+    with ctx, cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(fn, items))
 
 
 def _row_id(M: np.ndarray, k: int, rng: np.random.Generator, oversample: int = 10):
@@ -224,27 +229,61 @@ def _row_id(M: np.ndarray, k: int, rng: np.random.Generator, oversample: int = 1
     return sk, X
 
 
-def build_hss(w: Workload, far_samples: Optional[int] = None, mode: str = None,
-              clip: float = 1e-12) -> HSSMatrix:
+def _projected_block(w: Workload, pts_rows: np.ndarray, pts_cols: np.ndarray,
+                     Om_cols: np.ndarray, device: str) -> np.ndarray:
+    """K(rows, cols) @ Om_cols without forming K whole (torch, FP64, row chunks)."""
+    import torch
+    dev = torch.device(device)
+    xc = torch.as_tensor(pts_cols, dtype=torch.float64, device=dev)
+    om = torch.as_tensor(Om_cols, dtype=torch.float64, device=dev)
+    out = torch.empty((len(pts_rows), om.shape[1]), dtype=torch.float64, device=dev)
+    budget = (1 << 28) if dev.type == "cuda" else (1 << 23)
+    step = max(1, budget // max(1, len(pts_cols)))
+    for s0 in range(0, len(pts_rows), step):
+        xr = torch.as_tensor(pts_rows[s0:s0 + step], dtype=torch.float64, device=dev)
+        d = torch.cdist(xr, xc) if xr.shape[1] > 1 else (xr - xc.T).abs()
+        if w.kernel == "inv":
+            K = 1.0 / (d + 1e-3)
+        elif w.kernel == "exp":
+            K = torch.exp(-d / w.length)
+        elif w.kernel == "yukawa":
+            K = torch.exp(-d) / (d + 1e-3)
+        elif w.kernel == "poly2":
+            K = (1.0 + xr @ xc.T) ** 2
+        else:
+            raise ValueError(w.kernel)
+        out[s0:s0 + step] = K @ om
+    return out.cpu().numpy()
+
+
+def build_hss(w: Workload, far_samples: Optional[int] = None, mode: str = "spd",
+              clip: float = 1e-12, device: Optional[str] = None) -> HSSMatrix:
     """Compress the shifted kernel matrix of workload ``w`` into HSS form.
 
     ``mode="orth"``: orthonormal U and E (thin QR of the ID interpolation
-    matrices), S = R_c2 K(sk_c2, sk_c1) R_c1ᵀ.
-    ``mode="spd"``: the same skeletons, but every basis is normalised in the
-    metric of the Cholesky factor Λ of its diagonal block (scaling-and-
-    compression): W = orth(Λ⁻¹ X), U = Λ W (non-orthonormal), E = Λ_p W_p with
-    Λ_p = chol([[I, Sᵀ], [S, I]]), and the coupling S of every sibling pair is the
-    exact projection Ω_c2ᵀ A(I_c2, I_c1) Ω_c1 of the kernel block on the whitened
-    nested bases (O(N² r) work: meant for N up to ~65k).  Each such S has
-    2-norm < 1 (a block of an SPD matrix with identity diagonal blocks; the
-    singular values are clipped at 1 - clip against round-off), and the
+    matrices), S = R_c2 K(sk_c2, sk_c1) R_c1ᵀ.  Fast (O(N r) kernel
+    evaluations) but the compressed matrix loses definiteness once the
+    compression error exceeds the smallest eigenvalue.
+    ``mode="spd"`` (default): the same skeletons, but every basis is normalised
+    in the metric of the Cholesky factor Λ of its diagonal block (scaling-and-
+    compression): W = orth(Λ⁻¹ X) fitted by least squares in that metric,
+    U = Λ W (non-orthonormal), E = Λ_p W_p with Λ_p = chol([[I, Sᵀ], [S, I]]);
+    the coupling of every sibling pair is the exact projection
+    Ω_c2ᵀ A(I_c2, I_c1) Ω_c1 of the kernel block on the whitened nested bases
+    (Ω_leaf = Λ⁻ᵀ W, Ω_p = blkdiag(Ω_c1, Ω_c2) Λ_p⁻ᵀ W_p), an O(N² r) product
+    computed in row chunks with torch (on ``device``: the GPU when available).
+    Each S then has 2-norm < 1 (a block of an SPD matrix with identity diagonal
+    blocks; singular values are clipped at 1 - clip against round-off) and the
     assembled matrix is SPD by construction for any basis quality: at every
-    level it is Λ[(I - WWᵀ) + W H Wᵀ]Λᵀ with H the SPD matrix of the level above.  Leaf D blocks are the exact shifted kernel blocks in both modes.
-    The default is "spd" for the exponential covariance (tiny nugget) and
-    "orth" otherwise.
+    level it is Λ[(I - WWᵀ) + W H Wᵀ]Λᵀ with H the SPD matrix of the level above.
+    Leaf D blocks are the exact shifted kernel blocks in both modes.
     """
-    if mode is None:
-        mode = "spd" if w.kernel == "exp" else "orth"
+    if device is None:
+        try:
+            import torch
+            device = "cuda" if torch.cuda.is_available() else "cpu"
+        except Exception:  # pragma: no cover
+            device = "cpu"
     rng = np.random.default_rng(w.seed)
     pts0 = make_points(w, rng)
     L = w.levels
@@ -257,26 +296,24 @@ def build_hss(w: Workload, far_samples: Optional[int] = None, mode: str = None,
     r = w.rank
     if far_samples is None:
         far_samples = max(2 * r, 64)
-    crng = np.random.default_rng(w.seed + 7919)
 
     def node_range(l: int, i: int):
         span = 2 ** (L - l)
         return int(offs[i * span]), int(offs[(i + 1) * span])
 
     def clip_norm(X):
-        if mode != "spd":
-            return X
         u, sv, vt = np.linalg.svd(X)
         if sv.size and sv[0] > 1.0 - clip:
             X = (u * np.minimum(sv, 1.0 - clip)) @ vt
         return X
 
-    D = []
-    for i in range(2 ** L):
+    def leaf_block(i):
         a, b = offs[i], offs[i + 1]
         blk = kernel_block(w, pts[a:b], pts[a:b])
         blk[np.diag_indices_from(blk)] += w.shift
-        D.append(0.5 * (blk + blk.T))
+        return 0.5 * (blk + blk.T)
+
+    D = _parallel_map(leaf_block, range(2 ** L))
 
     ranks: Dict[int, np.ndarray] = {}
     U: List[np.ndarray] = []
@@ -285,92 +322,78 @@ def build_hss(w: Workload, far_samples: Optional[int] = None, mode: str = None,
     cand = [np.arange(offs[i], offs[i + 1]) for i in range(2 ** L)]
     skel: Dict[int, List[np.ndarray]] = {}
     Rfac: Dict[int, List[np.ndarray]] = {}
+    Om_prev = None
 
     for l in range(L, 0, -1):
         nn = 2 ** l
-        ranks[l] = np.zeros(nn, dtype=np.int64)
-        skel[l], Rfac[l] = [], []
-        if l < L:
-            E[l] = []
-        lam_w = []
-        for i in range(nn):
+
+        def compress(i, l=l, cand=cand):
+            nrng = np.random.default_rng([w.seed, 7919, l, i])
             sib = i ^ 1
             pa, pb = node_range(l - 1, i // 2)
             outside = n - (pb - pa)
             J = cand[sib]
             if outside > 0 and far_samples > 0:
-                far = crng.integers(0, outside, size=min(far_samples, outside))
+                far = nrng.integers(0, outside, size=min(far_samples, outside))
                 far = np.where(far < pa, far, far + (pb - pa))
                 J = np.concatenate([J, far])
             M = kernel_block(w, pts[cand[i]], pts[J])
-            sk, X = _row_id(M, r, crng)
-            ranks[l][i] = X.shape[1]
-            skel[l].append(cand[i][sk])
-            if l == L:
-                Rc = None
-                Y = X
-            else:
-                c1, c2 = 2 * i, 2 * i + 1
-                Rc = sla.block_diag(Rfac[l + 1][c1], Rfac[l + 1][c2])
+            sk, X = _row_id(M, r, nrng)
+            Rc = None
+            Y = X
+            if l < L:
+                Rc = sla.block_diag(Rfac[l + 1][2 * i], Rfac[l + 1][2 * i + 1])
                 Y = Rc @ X
+            lam_w = None
             if mode == "spd":
                 if l == L:
                     Lam = np.linalg.cholesky(D[i])
                 else:
                     Sc = S[l + 1][i]
                     r1, r2 = Sc.shape[1], Sc.shape[0]
-                    T = np.block([[np.eye(r1), Sc.T], [Sc, np.eye(r2)]])
-                    Lam = np.linalg.cholesky(T)
-                # fit the scaled rows Λ⁻¹ (Rc) M on the skeleton rows M[sk] by
-                # least squares, so the interpolation error is small in the
-                # scaled metric the definiteness argument uses
+                    Lam = np.linalg.cholesky(np.block([[np.eye(r1), Sc.T], [Sc, np.eye(r2)]]))
+                # least-squares fit of the scaled rows Λ⁻¹ (Rc) M on M[sk]
                 Ms = M if Rc is None else Rc @ M
                 Ms = sla.solve_triangular(Lam, Ms, lower=True)
                 Ysc = np.linalg.lstsq(M[sk].T, Ms.T, rcond=None)[0].T
                 Wq, R = np.linalg.qr(Ysc)
                 Q = Lam @ Wq
-                lam_w.append((Lam, Wq))
+                lam_w = (Lam, Wq)
             else:
                 Q, R = np.linalg.qr(Y)
-            if l == L:
-                U.append(Q)
-            else:
-                E[l].append(Q)
-            Rfac[l].append(R)
+            return cand[i][sk], X.shape[1], Q, R, lam_w
+
+        res = _parallel_map(compress, range(nn))
+        ranks[l] = np.array([x[1] for x in res], dtype=np.int64)
+        skel[l] = [x[0] for x in res]
+        Rfac[l] = [x[3] for x in res]
+        if l == L:
+            U = [x[2] for x in res]
+        else:
+            E[l] = [x[2] for x in res]
         S[l] = []
         if mode == "spd":
-            # whitened nested bases Ω (|I_i| x r): Ω_leaf = Λ⁻ᵀ W,
-            # Ω_p = blkdiag(Ω_c1, Ω_c2) Λ_p⁻ᵀ W_p; the coupling of a sibling
-            # pair is the exact projection Ω_c2ᵀ A(I_c2, I_c1) Ω_c1, a block of
-            # the SPD matrix Ωᵀ A Ω with identity diagonal blocks, so |S| < 1.
             newOm = []
             for i in range(nn):
-                Lam, Wq = lam_w[i]
+                Lam, Wq = res[i][4]
                 Om = sla.solve_triangular(Lam, Wq, lower=True, trans="T")
                 if l < L:
-                    Om = np.concatenate([Om_prev[2 * i] @ Om[:Om_prev[2 * i].shape[1]],
-                                         Om_prev[2 * i + 1] @ Om[Om_prev[2 * i].shape[1]:]])
+                    k1 = Om_prev[2 * i].shape[1]
+                    Om = np.concatenate([Om_prev[2 * i] @ Om[:k1], Om_prev[2 * i + 1] @ Om[k1:]])
                 newOm.append(Om)
             Om_prev = newOm
-        for k2 in range(nn // 2):
-            c1, c2 = 2 * k2, 2 * k2 + 1
-            if mode == "spd":
+            for k2 in range(nn // 2):
+                c1, c2 = 2 * k2, 2 * k2 + 1
                 a1, b1 = node_range(l, c1)
                 a2, b2 = node_range(l, c2)
-                acc = np.zeros((b2 - a2, Om_prev[c1].shape[1]))
-                step = max(1, (1 << 20) // max(1, b1 - a1))
-
-                def rows(s0, a1=a1, b1=b1, a2=a2, b2=b2, acc=acc, Om=Om_prev[c1]):
-                    s1 = min(b2, s0 + step)
-                    acc[s0 - a2:s1 - a2] = kernel_block(w, pts[s0:s1], pts[a1:b1]) @ Om
-
-                _parallel_map(rows, range(a2, b2, step))
+                acc = _projected_block(w, pts[a2:b2], pts[a1:b1], Om_prev[c1], device)
                 S[l].append(clip_norm(Om_prev[c2].T @ acc))
-            else:
+        else:
+            for k2 in range(nn // 2):
+                c1, c2 = 2 * k2, 2 * k2 + 1
                 Kss = kernel_block(w, pts[skel[l][c2]], pts[skel[l][c1]])
                 S[l].append(Rfac[l][c2] @ Kss @ Rfac[l][c1].T)
-        cand = [np.concatenate([skel[l][2 * p], skel[l][2 * p + 1]])
-                for p in range(nn // 2)]
+        cand = [np.concatenate([skel[l][2 * p], skel[l][2 * p + 1]]) for p in range(nn // 2)]
 
     return HSSMatrix(levels=L, sizes=sizes, ranks=ranks, D=D, U=U, E=E, S=S,
                      perm=perm, points=pts, workload=w)

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Per-step parity compares what the oracle computes node by node (basis
+completion Q and L_B, the factored block L^RR / L^SR / Â^SS, the merged basis of
+the next level) with the exported device arrays, on seeded inputs that span
+several 64-wide GEMM tiles and 32-wide Cholesky panels with ragged tails.
+End-to-end parity compares x (relative 1e-10 per column) and log det (relative
+1e-12 on the scale Σ|2 log l_jj|) with the oracle, plus the HSS matvec.
+Tolerances of the per-step arrays: both sides are FP64 Householder / Cholesky
+of the same matrices with the same sign convention, so they agree to a small
+multiple of b·ε relative to the block's norm.
+"""
+import numpy as np
+import pytest
+
+from oracle import ulv as O
+from paper_2311_00921_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2311_00921_gb300 import hss  # noqa: E402
+
+EPS = np.finfo(np.float64).eps
+
+
+def q_from_vt(V, T):
+    return np.eye(V.shape[0]) - V @ T @ V.T
+
+
+def check_close(a, b, tol, what):
+    scale = max(np.abs(b).max(), 1e-300)
+    err = np.abs(a - b).max() / scale
+    assert err <= tol, f"{what}: max rel err {err:.3e} > {tol:.1e}"
+
+
+def run_both(h, nrhs, seed=7):
+    dev = hss.HSS(h)
+    dev.factorize("fp64")
+    F = O.factor(h)
+    b = I.rhs(h.n, nrhs, seed)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    return dev, F, b, x
+
+
+def check_end_to_end(dev, F, b, x):
+    x_ref = O.solve(F, b).reshape(x.shape)
+    for j in range(x.shape[1] if x.ndim == 2 else 1):
+        xa = x[:, j] if x.ndim == 2 else x
+        xr = x_ref[:, j] if x.ndim == 2 else x_ref
+        err = np.linalg.norm(xa - xr) / np.linalg.norm(xr)
+        assert err <= 1e-10, f"column {j}: x rel err {err:.3e}"
+    ld, ld_ref = dev.logdet(), O.logdet(F)
+    scale = 2.0 * sum(np.abs(np.log(np.diag(L))).sum() for l in F.LRR for L in F.LRR[l]
+                      if L.size) + 2.0 * np.abs(np.log(np.diag(F.L0))).sum()
+    assert abs(ld - ld_ref) <= 1e-12 * scale, (ld, ld_ref)
+
+
+def check_steps(dev, F, h):
+    L = h.levels
+    for l in range(L, 0, -1):
+        V, T, LB, M = (dev.export(k, l) for k in ("V", "T", "LB", "M"))
+        for i in range(2 ** l):
+            b = V.shape[1]
+            r = V.shape[2]
+            c = b - r
+            tol = 50 * b * EPS
+            check_close(q_from_vt(V[i], T[i]), F.Q[l][i], tol, f"Q l={l} i={i}")
+            check_close(LB[i], F.LB[l][i], tol * 10, f"L_B l={l} i={i}")
+            Mi = M[i]
+            if c:
+                check_close(np.tril(Mi[:c, :c]), F.LRR[l][i], 1e-11, f"L^RR l={l} i={i}")
+                check_close(Mi[c:, :c], F.LSR[l][i], 1e-11, f"L^SR l={l} i={i}")
+            ss = np.tril(Mi[c:, c:])
+            check_close(ss, np.tril(F.SS[l][i]), 1e-11, f"SS l={l} i={i}")
+        if l < L:
+            B = dev.export("B", l)
+            for i in range(2 ** l):
+                check_close(B[i], F.Bnode[l][i], 1e-11, f"merged basis l={l} i={i}")
+
+
+# ---------------------------------------------------------------- per step
+@pytest.mark.parametrize("levels,leaf,rank,ortho", [
+    (3, 100, 13, False),     # ragged tiles and panels, non-orthonormal bases
+    (2, 64, 32, True),
+    (4, 96, 40, False),
+])
+def test_per_step_random(levels, leaf, rank, ortho):
+    h = I.random_hss(levels, leaf, rank, seed=levels * 31 + leaf, orthonormal=ortho)
+    dev, F, b, x = run_both(h, 3)
+    check_steps(dev, F, h)
+    check_end_to_end(dev, F, b, x)
+
+
+@pytest.mark.parametrize("name,n,kw", [
+    ("cube_inv_4k", 4096, {}),                              # the full workload
+    ("grid_exp_64k", 4096, {}),                             # scaled (spd construction)
+    ("sphere_yukawa_256k", 4096, {}),                       # scaled
+    ("sphere_yukawa_256k", 2048, {"leaf": 128, "rank": 48}),
+])
+def test_per_step_kernel_workloads(name, n, kw):
+    w = I.scaled(I.WORKLOADS[name], n, **kw)
+    h = I.build_hss(w)
+    dev, F, b, x = run_both(h, 4)
+    check_steps(dev, F, h)
+    check_end_to_end(dev, F, b, x)
+
+
+# ---------------------------------------------------------------- end to end
+@pytest.mark.parametrize("nrhs", [1, 16, 17, 35])
+def test_solve_rhs_chunks(nrhs):
+    w = I.scaled(I.WORKLOADS["cube_inv_4k"], 2048, leaf=128, rank=32)
+    h = I.build_hss(w)
+    dev, F, b, x = run_both(h, nrhs)
+    check_end_to_end(dev, F, b, x)
+
+
+def test_solve_in_place_and_vector():
+    h = I.random_hss(3, 48, 8, seed=2)
+    dev = hss.HSS(h)
+    dev.factorize("fp64")
+    F = O.factor(h)
+    b = I.rhs(h.n, 1, 3)[:, 0]
+    xb = hss.colmajor(b)
+    dev.solve(xb, xb)                       # x aliases b
+    np.testing.assert_allclose(xb.cpu().numpy(), O.solve(F, b), rtol=1e-10, atol=1e-14)
+
+
+def test_one_level_and_full_rank_leaves():
+    # L = 1 (two leaves + root) and rank = leaf (nothing eliminated at the leaves)
+    for levels, leaf, rank in [(1, 64, 16), (2, 32, 32)]:
+        h = I.random_hss(levels, leaf, rank, seed=11)
+        dev, F, b, x = run_both(h, 2)
+        check_steps(dev, F, h)
+        check_end_to_end(dev, F, b, x)
+
+
+def test_matches_dense_cholesky_exact_rank():
+    # exact-rank kernel: A_hss equals the kernel matrix, the GPU solve must too
+    w = I.Workload("poly", 16 * 2 ** 3, 16, 10, "cube", "poly2", 0.0, 3.0, 1, 21)
+    h = I.build_hss(w, mode="orth")
+    K = I.kernel_matrix(w, h.points)
+    dev = hss.HSS(h)
+    dev.factorize("fp64")
+    b = I.rhs(w.n, 2, 1)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    np.testing.assert_allclose(x, np.linalg.solve(K, b), rtol=1e-8, atol=1e-10)
+    assert abs(dev.logdet() - np.linalg.slogdet(K)[1]) <= 1e-10 * abs(np.linalg.slogdet(K)[1])
+
+
+@pytest.mark.parametrize("nrhs", [1, 5, 33])
+def test_matvec(nrhs):
+    h = I.random_hss(4, 80, 24, seed=5, orthonormal=False)
+    dev = hss.HSS(h)
+    x = I.rhs(h.n, nrhs, 9)
+    y = dev.matvec(hss.colmajor(x)).cpu().numpy()
+    y_ref = O.matvec(h, x).reshape(y.shape)
+    check_close(y, y_ref, 1e-13, "matvec")
+
+
+# ---------------------------------------------------------------- errors
+def test_not_spd_reports_level_and_node():
+    h = I.random_hss(3, 40, 8, seed=4)
+    h.D[5] = -h.D[5]
+    dev = hss.HSS(h)
+    dev.factorize("fp64")          # asynchronous: the error surfaces on sync
+    with pytest.raises(hss.HSSError) as ei:
+        dev.logdet()
+    assert ei.value.code == -3
+    info = dev.last_info()
+    assert info["code"] == -3 and info["level"] == 3 and info["node"] == 5
+    with pytest.raises(O.NotSPD) as eo:
+        O.factor(h)
+    assert (eo.value.level, eo.value.node, eo.value.col) == (3, 5, info["col"])
+
+
+def test_solve_before_factorize():
+    h = I.random_hss(2, 32, 4, seed=1)
+    dev = hss.HSS(h)
+    with pytest.raises(hss.HSSError) as ei:
+        dev.solve(hss.colmajor(np.ones(h.n)))
+    assert ei.value.code == -2
+
+
+# ---------------------------------------------------------------- full size, sampled
+@pytest.mark.slow
+def test_full_size_sphere_yukawa_sampled():
+    """N = 262,144 (leaf 512, rank 128, 9 levels, 16 right-hand sides): sampled
+    leaves' factor blocks against the oracle's node step, the backward error
+    through the oracle's matvec, and log det against the oracle's factorization."""
+    w = I.WORKLOADS["sphere_yukawa_256k"]
+    h = I.build_hss(w)
+    dev = hss.HSS(h)
+    dev.factorize("fp64")
+    b = I.rhs(w.n, w.nrhs, w.seed + 1)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    L = h.levels
+    V, T, M = dev.export("V", L), dev.export("T", L), dev.export("M", L)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(2 ** L, 6, replace=False):
+        Q, LB, Ah, LRR, LSR, SS = O.node_step(h.D[i], h.U[i])
+        c = LRR.shape[0]
+        check_close(q_from_vt(V[i], T[i]), Q, 50 * 512 * EPS, f"Q leaf {i}")
+        check_close(np.tril(M[i][:c, :c]), LRR, 1e-11, f"L^RR leaf {i}")
+        check_close(M[i][c:, :c], LSR, 1e-11, f"L^SR leaf {i}")
+        check_close(np.tril(M[i][c:, c:]), np.tril(SS), 1e-11, f"SS leaf {i}")
+    res = b - O.matvec(h, x)
+    rel = np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)
+    assert rel.max() <= 1e-13, rel.max()
+    F = O.factor(h)
+    ld_ref = O.logdet(F)
+    assert abs(dev.logdet() - ld_ref) <= 1e-12 * abs(ld_ref)
+    x_ref = O.solve(F, b)
+    err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    assert err.max() <= 1e-10, err.max()
