@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark of the HSS-ULV factor + solve on GB300.
+
+Workload: the N = 262,144 HSS matrix of the Yukawa kernel exp(-d)/(d + 1e-3)
+plus 64 I on points uniform on the unit sphere (leaf 512, rank 128, 9 levels),
+16 N(0,1) right-hand sides; seeded synthetic data in place of the paper's
+grids.  One step = one factorization (Alg. 2) + one solve of all right-hand
+sides.  ``value`` is the canonical-model TFLOP/s of that step (the paper's
+dense formulation: explicit Q, QᵀDQ as 4b³ per node), with inputs resident in
+HBM; ``e2e`` is the same metric through the C ABI from pinned host buffers,
+copies included.  Under torchrun each rank factors its own independent matrix
+(different seed) -- weak scaling, no collective on the data path.
+
+``--impl reference`` times the CPU oracle (NumPy/SciPy FP64, as it stands) on a
+bounded sample of the same workload: the subtree of one level-3 node (an HSS
+matrix of order 32,768 with the same leaf size, rank and kernel).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HSS-ULV factor+solve time & TFLOP/s, N=2^18: FP64 vs mixed+IR to 1e-12 residual"
+WORKLOAD = "sphere_yukawa_256k"
+SAMPLE_LEVEL = 3        # cpu baseline: subtree of one node of this level
+
+
+# ---------------------------------------------------------------- flop model
+def node_flops_canonical(b, r):
+    """Canonical per-node flops of the paper's dense formulation: Householder QR
+    of the basis, forming Q, QᵀDQ as two dense products, partial Cholesky."""
+    c = b - r
+    return (2 * b * r * r - 2.0 / 3 * r ** 3 + 4 * b * b * r - 4 * b * r * r + 4.0 / 3 * r ** 3
+            + 4 * b ** 3 + c ** 3 / 3.0 + r * c * c + r * (r + 1) * c)
+
+
+def factor_flops(levels, leaf, r):
+    f = (2 ** levels) * node_flops_canonical(leaf, r)
+    for l in range(1, levels):
+        f += (2 ** l) * node_flops_canonical(2 * r, r)
+    return f + (2 * r) ** 3 / 3.0
+
+
+def solve_flops(levels, leaf, r, nrhs):
+    def node(b):
+        c = b - r
+        return (4 * b * b + 2 * c * c + 4 * r * c) * nrhs
+    f = (2 ** levels) * node(leaf)
+    for l in range(1, levels):
+        f += (2 ** l) * node(2 * r)
+    return f + 2 * (2 * r) ** 2 * nrhs
+
+
+# ---------------------------------------------------------------- helpers
+def subtree(h, l0, p):
+    """The HSS generators of the subtree under node p of level l0 (the principal
+    submatrix A(I_p, I_p)); pure slicing."""
+    from paper_2311_00921_gb300.inputs import HSSMatrix
+    L = h.levels
+    Ls = L - l0
+    lo, hi = p * 2 ** Ls, (p + 1) * 2 ** Ls
+    E = {m: h.E[l0 + m][p * 2 ** m:(p + 1) * 2 ** m] for m in range(1, Ls)}
+    S = {m: h.S[l0 + m][p * 2 ** (m - 1):(p + 1) * 2 ** (m - 1)] for m in range(1, Ls + 1)}
+    ranks = {m: h.ranks[l0 + m][p * 2 ** m:(p + 1) * 2 ** m] for m in range(1, Ls + 1)}
+    return HSSMatrix(levels=Ls, sizes=h.sizes[lo:hi], ranks=ranks, D=h.D[lo:hi], U=h.U[lo:hi],
+                     E=E, S=S)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_fp64_peak(torch):
+    """cuBLAS DGEMM 8192^3 throughput (TFLOP/s), best of 3, in this run."""
+    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    b = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    a @ b
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2 * 8192 ** 3 / best / 1e12
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    if the kernel source changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(x.split("=", 1) for x in line.split())
+        if kv.get("kernel") != kernel:
+            continue
+        src = os.path.join(ROOT, "paper_2311_00921_gb300", "csrc", kv["src"])
+        if not os.path.exists(src):
+            return None
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != kv.get("src_sha"):
+            return None
+        return float(kv["bytes_per_launch"]) * float(kv.get("scale", 1.0))
+    return None
+
+
+KERNEL_SOURCES = {"gemm": "gemm_tile_kernel", "syr2k": "syr2k_lower_kernel",
+                  "pchol": "pchol_kernel", "ql": "ql_basis_kernel",
+                  "gemm_skinny": "gemm_skinny_kernel", "trsv_fwd": "trsv_fwd_kernel",
+                  "trsv_bwd": "trsv_bwd_kernel", "other": "logdet_reduce_kernel"}
+
+
+def workload(args):
+    from paper_2311_00921_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    if args.n and args.n != w.n:
+        w = I.scaled(w, args.n)
+    return w
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+def oracle_sample(h, nrhs, seed):
+    """Time the oracle's factor + solve on the level-3 subtree; returns
+    (seconds, canonical flops of that sample)."""
+    from oracle import ulv as O
+    from paper_2311_00921_gb300 import inputs as I
+    hs = subtree(h, SAMPLE_LEVEL, 0)
+    b = I.rhs(hs.n, nrhs, seed)
+    t0 = time.perf_counter()
+    F = O.factor(hs)
+    O.solve(F, b)
+    dt = time.perf_counter() - t0
+    fl = factor_flops(hs.levels, h.leaf, h.rank) + solve_flops(hs.levels, h.leaf, h.rank, nrhs)
+    return dt, fl, hs.n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2311_00921_gb300 import inputs as I
+    w = workload(args)
+    h = I.build_hss(w)
+    for _ in range(args.warmup):
+        oracle_sample(h, w.nrhs, w.seed + 1)
+    tot_t, tot_f = 0.0, 0.0
+    n_s = 0
+    for _ in range(args.steps):
+        dt, fl, n_s = oracle_sample(h, w.nrhs, w.seed + 1)
+        tot_t += dt
+        tot_f += fl
+    val = tot_f / tot_t / 1e12
+    sample = (f"oracle factor+solve of the subtree under one level-{SAMPLE_LEVEL} node "
+              f"(N={n_s}, leaf {w.leaf}, rank {w.rank}, {w.nrhs} rhs) of the {w.name} matrix")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * tot_t / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "rank": w.rank,
+                      "levels": w.levels, "nrhs": w.nrhs, "precision": "fp64"},
+           "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    from paper_2311_00921_gb300 import hss, inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    base = workload(args)
+    import dataclasses
+    w = dataclasses.replace(base, seed=base.seed + 10 * rank)
+    h = I.build_hss(w)
+    dev = hss.HSS(h)
+    b_host = I.rhs(w.n, w.nrhs, w.seed + 1)
+    b = hss.colmajor(b_host)
+    x = torch.empty((w.nrhs, w.n), dtype=torch.float64, device="cuda").t()
+    prec = args.precision
+
+    def step():
+        dev.factorize(prec)
+        dev.solve(b, x)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # factor / solve split (untimed pass)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    dev.factorize(prec)
+    e[1].record()
+    dev.solve(b, x)
+    e[2].record()
+    torch.cuda.synchronize()
+    factor_ms, solve_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    peak = measured_fp64_peak(torch) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dev.trace(True)
+    l0 = dev.launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    launches = dev.launch_count() - l0
+    tr = dev.trace_read()
+    dev.trace(False)
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+
+    # correctness of the timed result (FP64 residual through the HSS matvec)
+    r = b - dev.matvec(x)
+    rel = (torch.linalg.vector_norm(r, dim=0) / torch.linalg.vector_norm(b, dim=0)).max().item()
+    logdet = dev.logdet()
+
+    fl_step = factor_flops(w.levels, w.leaf, w.rank) + solve_flops(w.levels, w.leaf, w.rank,
+                                                                    w.nrhs)
+    value = world * fl_step / (ms_step / 1e3) / 1e12
+
+    # dominant kernel by device time over the timed region
+    dom = max(tr, key=lambda k: tr[k][0])
+    dms, dn, dfl = tr[dom]
+    achieved = dfl / (dms / 1e3) / 1e12 if dms > 0 else 0.0
+    kname = KERNEL_SOURCES[dom]
+    traffic = traffic_record(kname)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None,
+                "traffic": traffic, "kernel": kname,
+                "peak_source": "cuBLAS DGEMM 8192^3 (FP64 pipe) measured in this run",
+                "kernel_ms_per_launch": dms / max(1, dn),
+                "kernel_share": dms / sum(v[0] for v in tr.values()),
+                "per_kernel_ms_per_step": {k: v[0] / args.steps for k, v in tr.items()},
+                "per_kernel_tflops": {k: (v[2] / (v[0] / 1e3) / 1e12 if v[0] else 0.0)
+                                      for k, v in tr.items()}}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, h, w, b_host, prec, fl_step, world, dist)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        dt, fl, n_s = oracle_sample(h, w.nrhs, w.seed + 1)
+        cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"oracle FP64 factor+solve of the subtree under one level-{SAMPLE_LEVEL}"
+                         f" node (N={n_s}, same leaf/rank/kernel, {w.nrhs} rhs), "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if prec == "fp64" else f"{prec}+f64",
+               "data": "synthetic",
+               "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "rank": w.rank,
+                          "levels": w.levels, "nrhs": w.nrhs, "precision": prec,
+                          "parallelism": f"replicas{world}" if world > 1 else "single",
+                          "l2": "HSS data (1.54 GB) and factors exceed L2; no flush",
+                          "flop_model": "canonical dense-QtDQ model per node (4b^3 + form-Q "
+                                        "+ QR + partial Cholesky) + solve (4b^2+2c^2+4rc) "
+                                        "per rhs"},
+               "factor_ms": factor_ms, "solve_ms": solve_ms,
+               "check": {"max_rel_residual": rel, "logdet": logdet},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
+               "gpu_launches": launches}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, h, w, b_host, prec, fl_step, world, dist):
+    """One user call sequence per step from pinned host memory: create the object
+    (H2D of the generators), factor, upload b, solve, read x back, destroy."""
+    import torch
+    from paper_2311_00921_gb300 import hss
+    import ctypes
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t
+
+    D = pinned(hss._colmajor_blocks(h.D))
+    U = pinned(hss._colmajor_blocks(h.U))
+    E = pinned(np.concatenate([hss._colmajor_blocks(h.E[l]).ravel()
+                               for l in range(1, h.levels)]))
+    S = pinned(np.concatenate([hss._colmajor_blocks(h.S[l]).ravel()
+                               for l in range(1, h.levels + 1)]))
+    bh = pinned(np.asfortranarray(b_host).T.copy())     # (nrhs, n) rows = columns of b
+    xh = torch.empty_like(bh).pin_memory()
+    lib = hss.load()
+    h2d = (D.numel() + U.numel() + E.numel() + S.numel() + bh.numel()) * 8
+    d2h = xh.numel() * 8
+    bd = torch.empty_like(bh, device="cuda")
+    xd = torch.empty_like(bh, device="cuda")
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        shape = hss.Shape(w.n, w.leaf, w.rank, w.levels)
+        out = ctypes.c_void_p()
+        hss._check(lib.hss_create(ctypes.byref(shape), D.data_ptr(), U.data_ptr(), E.data_ptr(),
+                                  S.data_ptr(), 0, ctypes.byref(out)), "hss_create")
+        st = torch.cuda.current_stream()
+        opt = hss.Options(hss.PRECISIONS[prec], 30, 1e-12)
+        hss._check(lib.hss_factorize(out, ctypes.byref(opt), st.cuda_stream), "hss_factorize")
+        bd.copy_(bh, non_blocking=True)
+        hss._check(lib.hss_solve(out, bd.data_ptr(), xd.data_ptr(), w.nrhs, w.n, st.cuda_stream),
+                   "hss_solve")
+        xh.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        lib.hss_destroy(out)
+    dt = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    return {"value": world * fl_step * steps / dt / 1e12, "unit": "TFLOP/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": 1e3 * dt / steps, "steps": steps,
+            "includes": "hss_create from pinned host (generators H2D), factorize, b H2D, "
+                        "solve, x D2H, hss_destroy"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16", "fp32"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--n", type=int, default=0,
+                    help="scale the workload to this order (same leaf, rank, kernel)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

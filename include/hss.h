@@ -144,6 +144,33 @@ int hss_last_info(hss_t h, int32_t* level, int32_t* node, int32_t* col, int32_t*
  * factor is not FP64. */
 int hss_export(hss_t h, int32_t what, int32_t level, double* dst, size_t count);
 
+/* Kernel classes reported by the tracer (one per kernel function). */
+typedef enum {
+  HSS_K_QL = 0,        /* basis completion (Householder QL + compact-WY T) */
+  HSS_K_GEMM = 1,      /* batched GEMM, 64x64 tiles (diagonal product, merge) */
+  HSS_K_GEMM_SKINNY = 2, /* batched GEMM with <= 32 columns (solve, matvec) */
+  HSS_K_SYR2K = 3,     /* lower-triangle rank-2k update (diagonal product) */
+  HSS_K_PCHOL = 4,     /* partial Cholesky + merge epilogue, root Cholesky */
+  HSS_K_TRSV_FWD = 5,  /* forward triangular sweep of the solve */
+  HSS_K_TRSV_BWD = 6,  /* backward triangular sweep of the solve */
+  HSS_K_OTHER = 7,     /* log-det reduction and small helpers */
+  HSS_K_COUNT = 8
+} hss_kernel_kind;
+
+/* Per-kernel timing: with enable = 1 every later launch of the object is
+ * bracketed by two CUDA events on its launch stream and logged with its
+ * algorithmic flop count (the operation's definition, not the executed
+ * instructions); enable = 0 stops logging.  Enabling clears the log. */
+int hss_trace(hss_t h, int32_t enable);
+
+/* Sum of the logged launches of one kernel class: total device milliseconds,
+ * number of launches and algorithmic flops.  Synchronizes the logged streams.
+ * Errors: INVALID_ARG. */
+int hss_trace_read(hss_t h, int32_t kind, double* ms, int64_t* launches, double* flops);
+
+/* Number of kernel launches the object has issued since creation. */
+int hss_launch_count(hss_t h, int64_t* out);
+
 /* Free the object and its device memory. NULL is ignored. */
 void hss_destroy(hss_t h);
 

@@ -54,6 +54,15 @@ struct hss_s {
   cudaStream_t last_stream = nullptr;
   int ir_iters = 0;
   double ir_resid = 0.0;
+  // launch accounting and the optional per-launch event log
+  long long launches = 0;
+  int tracing = 0;
+  struct Rec {
+    int kind;
+    double flops;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> trace;
 };
 
 namespace {
@@ -130,9 +139,65 @@ size_t layout(hss_s* h, char* base) {
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? HSS_OK : HSS_ERR_CUDA; }
 
+// Brackets one kernel launch: counts it and, when tracing, logs two events.
+struct Launch {
+  hss_s* h;
+  cudaStream_t st;
+  hss_s::Rec rec{};
+  bool on = false;
+  Launch(hss_s* h_, int kind, double flops, cudaStream_t st_) : h(h_), st(st_) {
+    ++h->launches;
+    if (h->tracing) {
+      rec.kind = kind;
+      rec.flops = flops;
+      if (cudaEventCreate(&rec.a) == cudaSuccess && cudaEventCreate(&rec.b) == cudaSuccess) {
+        cudaEventRecord(rec.a, st);
+        on = true;
+      }
+    }
+  }
+  ~Launch() {
+    if (on) {
+      cudaEventRecord(rec.b, st);
+      h->trace.push_back(rec);
+    }
+  }
+};
+
+void clear_trace(hss_s* h) {
+  for (auto& r : h->trace) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  h->trace.clear();
+}
+
+double gemm_flops(int m, int n, int k, int batch) { return 2.0 * m * n * (double)k * batch; }
+
+void gemm(hss_s* h, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
+          long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc,
+          long long sC, int batch, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return;
+  Launch l(h, n <= 32 ? HSS_K_GEMM_SKINNY : HSS_K_GEMM, gemm_flops(m, n, k, batch), st);
+  gemm_batched<double>(ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+                       st);
+}
+
 int check_launch() {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HSS_OK : HSS_ERR_CUDA;
+}
+
+// partial Cholesky of the first c of b columns: POTRF c x c, TRSM (b-c) x c,
+// SYRK (b-c) x (b-c) with depth c
+double pchol_flops(int b, int c) {
+  const double r = b - c;
+  return (double)c * c * c / 3.0 + r * c * c + r * (r + 1.0) * c;
+}
+
+// triangular sweep of one node: c x c triangle plus the (b-c) x c block
+double trsv_flops(int b, int c, int nrhs) {
+  return ((double)c * c + 2.0 * (b - c) * c) * nrhs;
 }
 
 // Q application on a level vector: vec_seg := vec_seg - V op(T) (Vᵀ vec_seg)
@@ -141,11 +206,11 @@ void apply_q(hss_s* h, const Level& P, double* vec, int ldv, int nc, bool transp
              cudaStream_t st) {
   const int b = P.b, r = P.r, n = P.n;
   const long long s1 = (long long)r * kMaxCols;
-  gemm_batched<double>(true, false, r, nc, b, 1.0, P.V, b, (long long)b * r, vec, ldv, b, 0.0,
+  gemm(h, true, false, r, nc, b, 1.0, P.V, b, (long long)b * r, vec, ldv, b, 0.0,
                        h->t1, r, s1, n, st);
-  gemm_batched<double>(transpose, false, r, nc, r, 1.0, P.T, r, (long long)r * r, h->t1, r, s1,
+  gemm(h, transpose, false, r, nc, r, 1.0, P.T, r, (long long)r * r, h->t1, r, s1,
                        0.0, h->t2, r, s1, n, st);
-  gemm_batched<double>(false, false, b, nc, r, -1.0, P.V, b, (long long)b * r, h->t2, r, s1, 1.0,
+  gemm(h, false, false, b, nc, r, -1.0, P.V, b, (long long)b * r, h->t2, r, s1, 1.0,
                        vec, ldv, b, n, st);
 }
 
@@ -160,51 +225,66 @@ int factorize_fp64(hss_s* h, cudaStream_t st) {
     const long long br = (long long)b * r, bb = (long long)b * b;
     // (a) basis completion (Eq. 2-3)
     const double* Bsrc = (l == L) ? h->U : P.B;
-    launch_ql_basis<double>(Bsrc, b, br, P.V, br, P.T, rr, P.LB, rr, b, r, n, st);
+    {
+      Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, st);
+      launch_ql_basis<double>(Bsrc, b, br, P.V, br, P.T, rr, P.LB, rr, b, r, n, st);
+    }
     // (d, first half) merge: rescaled coupling Ŝ = L_B(c2) S L_B(c1)ᵀ into the
     // parent's off-diagonal blocks, parent basis blkdiag(L_B(c1), L_B(c2)) E_p
     const int np = n / 2;
     const double* Sl = h->S + h->Soff[l];
     const int ldq = 2 * r;
     const long long sq = 4 * rr;
-    gemm_batched<double>(false, false, r, r, r, 1.0, P.LB + rr, r, 2 * rr, Sl, r, rr, 0.0, h->Z, r,
+    gemm(h, false, false, r, r, r, 1.0, P.LB + rr, r, 2 * rr, Sl, r, rr, 0.0, h->Z, r,
                          rr, np, st);
-    gemm_batched<double>(false, true, r, r, r, 1.0, h->Z, r, rr, P.LB, r, 2 * rr, 0.0, Q.A + r, ldq,
+    gemm(h, false, true, r, r, r, 1.0, h->Z, r, rr, P.LB, r, 2 * rr, 0.0, Q.A + r, ldq,
                          sq, np, st);
-    gemm_batched<double>(false, true, r, r, r, 1.0, P.LB, r, 2 * rr, h->Z, r, rr, 0.0,
+    gemm(h, false, true, r, r, r, 1.0, P.LB, r, 2 * rr, h->Z, r, rr, 0.0,
                          Q.A + (long long)r * ldq, ldq, sq, np, st);
     if (l - 1 >= 1) {
       const double* Ep = h->E + h->Eoff[l - 1];
-      gemm_batched<double>(false, false, r, r, r, 1.0, P.LB, r, 2 * rr, Ep, 2 * r, 2 * rr, 0.0,
+      gemm(h, false, false, r, r, r, 1.0, P.LB, r, 2 * rr, Ep, 2 * r, 2 * rr, 0.0,
                            Q.B, 2 * r, 2 * rr, np, st);
-      gemm_batched<double>(false, false, r, r, r, 1.0, P.LB + rr, r, 2 * rr, Ep + r, 2 * r, 2 * rr,
+      gemm(h, false, false, r, r, r, 1.0, P.LB + rr, r, 2 * rr, Ep + r, 2 * r, 2 * rr,
                            0.0, Q.B + r, 2 * r, 2 * rr, np, st);
     }
     // (b) diagonal product Â = Qᵀ A Q with Q = I - V T Vᵀ, in the symmetric
     // compact-WY form Â = A - Y'Vᵀ - V Y'ᵀ, Y' = A V T - ½ V Tᵀ Vᵀ A V T
     const double* Ain = (l == L) ? h->D : P.A;
-    gemm_batched<double>(false, false, b, r, b, 1.0, Ain, b, bb, P.V, b, br, 0.0, h->W, b, br, n,
+    gemm(h, false, false, b, r, b, 1.0, Ain, b, bb, P.V, b, br, 0.0, h->W, b, br, n,
                          st);
-    gemm_batched<double>(false, false, b, r, r, 1.0, h->W, b, br, P.T, r, rr, 0.0, h->Y, b, br, n,
+    gemm(h, false, false, b, r, r, 1.0, h->W, b, br, P.T, r, rr, 0.0, h->Y, b, br, n,
                          st);
-    gemm_batched<double>(true, false, r, r, b, 1.0, P.V, b, br, h->Y, b, br, 0.0, h->X, r, rr, n,
+    gemm(h, true, false, r, r, b, 1.0, P.V, b, br, h->Y, b, br, 0.0, h->X, r, rr, n,
                          st);
-    gemm_batched<double>(true, false, r, r, r, 1.0, P.T, r, rr, h->X, r, rr, 0.0, h->Z, r, rr, n,
+    gemm(h, true, false, r, r, r, 1.0, P.T, r, rr, h->X, r, rr, 0.0, h->Z, r, rr, n,
                          st);
-    gemm_batched<double>(false, false, b, r, r, -0.5, P.V, b, br, h->Z, r, rr, 1.0, h->Y, b, br, n,
+    gemm(h, false, false, b, r, r, -0.5, P.V, b, br, h->Z, r, rr, 1.0, h->Y, b, br, n,
                          st);
-    syr2k_lower_batched<double>(b, r, Ain, b, bb, h->Y, b, br, P.V, b, br, P.M, b, bb, n, st);
+    {
+      Launch k(h, HSS_K_SYR2K, 2.0 * r * b * (b + 1.0) * n, st);
+      syr2k_lower_batched<double>(b, r, Ain, b, bb, h->Y, b, br, P.V, b, br, P.M, b, bb, n, st);
+    }
     // (c) partial Cholesky + (d, second half) Schur complements into the parent
-    launch_pchol<double>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1), l, 0,
-                         h->status, n, st);
+    {
+      Launch k(h, HSS_K_PCHOL, pchol_flops(b, c) * n, st);
+      launch_pchol<double>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1), l,
+                           0, h->status, n, st);
+    }
     int rc = check_launch();
     if (rc) return rc;
   }
   // root Cholesky (Alg. 2 line 6)
   Level& R0 = h->lv[0];
-  launch_pchol<double>(R0.A, R0.b, (long long)R0.b * R0.b, R0.b, R0.b, nullptr, 0, 0,
-                       h->logdet_part, 0, 0, h->status, 1, st);
-  launch_logdet_reduce(h->logdet_part, (int)((2LL << L) - 1), h->logdet_val, st);
+  {
+    Launch k(h, HSS_K_PCHOL, pchol_flops(R0.b, R0.b), st);
+    launch_pchol<double>(R0.A, R0.b, (long long)R0.b * R0.b, R0.b, R0.b, nullptr, 0, 0,
+                         h->logdet_part, 0, 0, h->status, 1, st);
+  }
+  {
+    Launch k(h, HSS_K_OTHER, (double)((2LL << L) - 1), st);
+    launch_logdet_reduce(h->logdet_part, (int)((2LL << L) - 1), h->logdet_val, st);
+  }
   return check_launch();
 }
 
@@ -220,20 +300,34 @@ int solve_fp64(hss_s* h, double* x, int nrhs, int ld, cudaStream_t st) {
       double* vec = (l == L) ? xc : P.yv;
       const int ldv = (l == L) ? ld : P.n * P.b;
       apply_q(h, P, vec, ldv, nc, /*transpose=*/true, st);
-      launch_trsv_fwd<double>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                              Q.n * Q.b, r, P.n, st);
+      {
+        Launch k(h, HSS_K_TRSV_FWD, trsv_flops(P.b, P.c, nc) * P.n, st);
+        launch_trsv_fwd<double>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                                Q.n * Q.b, r, P.n, st);
+      }
     }
     Level& R0 = h->lv[0];
-    launch_trsv_fwd<double>(R0.A, R0.b, 0, R0.b, R0.b, R0.yv, R0.b, 0, nc, nullptr, 0, 0, 1, st);
-    launch_trsv_bwd<double>(R0.A, R0.b, 0, R0.b, R0.b, R0.yv, R0.b, 0, nc, nullptr, 0, 0, 1, st);
+    {
+      Launch k(h, HSS_K_TRSV_FWD, trsv_flops(R0.b, R0.b, nc), st);
+      launch_trsv_fwd<double>(R0.A, R0.b, 0, R0.b, R0.b, R0.yv, R0.b, 0, nc, nullptr, 0, 0, 1,
+                              st);
+    }
+    {
+      Launch k(h, HSS_K_TRSV_BWD, trsv_flops(R0.b, R0.b, nc), st);
+      launch_trsv_bwd<double>(R0.A, R0.b, 0, R0.b, R0.b, R0.yv, R0.b, 0, nc, nullptr, 0, 0, 1,
+                              st);
+    }
     // backward sweep, root -> leaves
     for (int l = 1; l <= L; ++l) {
       Level& P = h->lv[l];
       Level& Q = h->lv[l - 1];
       double* vec = (l == L) ? xc : P.yv;
       const int ldv = (l == L) ? ld : P.n * P.b;
-      launch_trsv_bwd<double>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                              Q.n * Q.b, r, P.n, st);
+      {
+        Launch k(h, HSS_K_TRSV_BWD, trsv_flops(P.b, P.c, nc) * P.n, st);
+        launch_trsv_bwd<double>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                                Q.n * Q.b, r, P.n, st);
+      }
       apply_q(h, P, vec, ldv, nc, /*transpose=*/false, st);
     }
     int rc = check_launch();
@@ -251,12 +345,12 @@ int matvec_fp64(hss_s* h, const double* x, double* y, int nrhs, int ld, cudaStre
     const double* xc = x + (long long)j0 * ld;
     double* yc = y + (long long)j0 * ld;
     // up-sweep: x̂_L = Uᵀ x, x̂_l = E_lᵀ [x̂_{l+1}(2p); x̂_{l+1}(2p+1)]
-    gemm_batched<double>(true, false, r, nc, leaf, 1.0, h->U, leaf, (long long)leaf * r, xc, ld,
+    gemm(h, true, false, r, nc, leaf, 1.0, h->U, leaf, (long long)leaf * r, xc, ld,
                          leaf, 0.0, h->lv[L].xh, nL * r, r, nL, st);
     for (int l = L - 1; l >= 1; --l) {
       Level& P = h->lv[l];
       Level& C = h->lv[l + 1];
-      gemm_batched<double>(true, false, r, nc, 2 * r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, C.xh,
+      gemm(h, true, false, r, nc, 2 * r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, C.xh,
                            C.n * r, 2 * r, 0.0, P.xh, P.n * r, r, P.n, st);
     }
     // sibling couplings of every level
@@ -264,22 +358,22 @@ int matvec_fp64(hss_s* h, const double* x, double* y, int nrhs, int ld, cudaStre
       Level& P = h->lv[l];
       const double* Sl = h->S + h->Soff[l];
       const int ldl = P.n * r;
-      gemm_batched<double>(false, false, r, nc, r, 1.0, Sl, r, rr, P.xh, ldl, 2 * r, 0.0, P.yh + r,
+      gemm(h, false, false, r, nc, r, 1.0, Sl, r, rr, P.xh, ldl, 2 * r, 0.0, P.yh + r,
                            ldl, 2 * r, P.n / 2, st);
-      gemm_batched<double>(true, false, r, nc, r, 1.0, Sl, r, rr, P.xh + r, ldl, 2 * r, 0.0, P.yh,
+      gemm(h, true, false, r, nc, r, 1.0, Sl, r, rr, P.xh + r, ldl, 2 * r, 0.0, P.yh,
                            ldl, 2 * r, P.n / 2, st);
     }
     // down-sweep: ŷ_{l+1}(children) += E_l ŷ_l
     for (int l = 1; l <= L - 1; ++l) {
       Level& P = h->lv[l];
       Level& C = h->lv[l + 1];
-      gemm_batched<double>(false, false, 2 * r, nc, r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, P.yh,
+      gemm(h, false, false, 2 * r, nc, r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, P.yh,
                            P.n * r, r, 1.0, C.yh, C.n * r, 2 * r, P.n, st);
     }
     // leaves: y = D x + U ŷ
-    gemm_batched<double>(false, false, leaf, nc, leaf, 1.0, h->D, leaf, (long long)leaf * leaf, xc,
+    gemm(h, false, false, leaf, nc, leaf, 1.0, h->D, leaf, (long long)leaf * leaf, xc,
                          ld, leaf, 0.0, yc, ld, leaf, nL, st);
-    gemm_batched<double>(false, false, leaf, nc, r, 1.0, h->U, leaf, (long long)leaf * r,
+    gemm(h, false, false, leaf, nc, r, 1.0, h->U, leaf, (long long)leaf * r,
                          h->lv[L].yh, nL * r, r, 1.0, yc, ld, leaf, nL, st);
     int rc = check_launch();
     if (rc) return rc;
@@ -363,6 +457,7 @@ void hss_destroy(hss_t h) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
+  clear_trace(h);
   cudaFree(h->arena);
   cudaSetDevice(cur);
   delete h;
@@ -439,6 +534,41 @@ int hss_last_info(hss_t h, int32_t* level, int32_t* node, int32_t* col, int32_t*
   if (ir_iters) *ir_iters = h->ir_iters;
   if (ir_resid) *ir_resid = h->ir_resid;
   return rc;
+}
+
+int hss_trace(hss_t h, int32_t enable) {
+  if (!h) return HSS_ERR_INVALID_ARG;
+  if (enable) {
+    for (auto& r : h->trace) cudaEventSynchronize(r.b);
+    clear_trace(h);
+  }
+  h->tracing = enable ? 1 : 0;
+  return HSS_OK;
+}
+
+int hss_trace_read(hss_t h, int32_t kind, double* ms, int64_t* launches, double* flops) {
+  if (!h || kind < 0 || kind >= HSS_K_COUNT) return HSS_ERR_INVALID_ARG;
+  double tot = 0.0, fl = 0.0;
+  long long cnt = 0;
+  for (auto& r : h->trace) {
+    if (r.kind != kind) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return HSS_ERR_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return HSS_ERR_CUDA;
+    tot += t;
+    fl += r.flops;
+    ++cnt;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = cnt;
+  if (flops) *flops = fl;
+  return HSS_OK;
+}
+
+int hss_launch_count(hss_t h, int64_t* out) {
+  if (!h || !out) return HSS_ERR_INVALID_ARG;
+  *out = h->launches;
+  return HSS_OK;
 }
 
 int hss_export(hss_t h, int32_t what, int32_t level, double* dst, size_t count) {

@@ -45,6 +45,10 @@ SIGNATURES = {
     "hss_sync": (_c_int, [_p]),
     "hss_last_info": (_c_int, [_p, _i32p, _i32p, _i32p, _i32p, ctypes.POINTER(_c_double)]),
     "hss_export": (_c_int, [_p, ctypes.c_int32, ctypes.c_int32, _p, ctypes.c_size_t]),
+    "hss_trace": (_c_int, [_p, ctypes.c_int32]),
+    "hss_trace_read": (_c_int, [_p, ctypes.c_int32, ctypes.POINTER(_c_double),
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_double)]),
+    "hss_launch_count": (_c_int, [_p, ctypes.POINTER(ctypes.c_int64)]),
     "hss_destroy": (None, [_p]),
     "hss_strerror": (ctypes.c_char_p, [_c_int]),
 }
@@ -193,6 +197,26 @@ class HSS:
                                     ctypes.byref(col), ctypes.byref(it), ctypes.byref(res))
         return {"code": code, "level": lvl.value, "node": node.value, "col": col.value,
                 "ir_iters": it.value, "ir_resid": res.value}
+
+    KERNELS = ("ql", "gemm", "gemm_skinny", "syr2k", "pchol", "trsv_fwd", "trsv_bwd", "other")
+
+    def trace(self, enable: bool):
+        _check(load().hss_trace(self._h, 1 if enable else 0), "hss_trace")
+
+    def trace_read(self):
+        """{kernel: (ms, launches, algorithmic flops)} of the logged launches."""
+        out = {}
+        for k, name in enumerate(self.KERNELS):
+            ms, n, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+            _check(load().hss_trace_read(self._h, k, ctypes.byref(ms), ctypes.byref(n),
+                                         ctypes.byref(fl)), "hss_trace_read")
+            out[name] = (ms.value, n.value, fl.value)
+        return out
+
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().hss_launch_count(self._h, ctypes.byref(v)), "hss_launch_count")
+        return v.value
 
     def export(self, what: str, level: int) -> np.ndarray:
         """Per-level factor arrays as (nodes, rows, cols) host arrays."""
