@@ -51,6 +51,7 @@ extern "C" {
 #define HSS_ERR_OOM (-5)            /* device allocation failed */
 #define HSS_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
 #define HSS_ERR_NO_CONVERGENCE (-7) /* iterative refinement hit its iteration limit */
+#define HSS_ERR_TOO_LARGE (-8)      /* problem exceeds the fixed scratch of hss_matvec_noalloc */
 
 typedef struct hss_s* hss_t;
 
@@ -120,6 +121,32 @@ int hss_logdet(hss_t h, double* out);
  * pass, leaf blocks.  FP64.  x and y are device pointers (n x nrhs, ld), must
  * not overlap.  Asynchronous.  Needs no factorization. */
 int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, void* stream);
+
+/* y = A x like hss_matvec, but allocating nothing: no cudaMalloc, no cudaFree,
+ * no allocating library call.  The paper has no counterpart; this entry point
+ * exists for callers that must not allocate device memory at call time -- for
+ * example a host application that reserves the whole device up front for its
+ * own memory pool, or a latency-critical loop in which a cudaMalloc (which can
+ * synchronize the device) is not acceptable.  Such callers cannot use
+ * hss_create, which allocates the object's arena.
+ *   shape, D, U, E, S: the generators in the packed layout of hss_create, as
+ *     DEVICE pointers on the current device, owned by the caller and only read.
+ *   x, y: device pointers, n x nrhs column-major with leading dimension ld;
+ *     they must not overlap.
+ * The per-level intermediate vectors live in one static device array of
+ * 2^21 doubles (16 MiB) that every device which loads the library holds until
+ * the process exits.  A problem fits when 2 (2^(levels+1) - 2) rank <= 2^21
+ * (one right-hand-side column); larger ones return HSS_ERR_TOO_LARGE before any
+ * device work.  Columns are processed in passes of as many as fit (at most 32).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * shares the one array and overwrites all of the part it reads, so no state
+ * carries over between calls -- but two calls that overlap on the GPU (other
+ * streams, other host threads) race on it: serialize them.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, TOO_LARGE, CUDA. */
+int hss_matvec_noalloc(const hss_shape* shape, const double* D, const double* U, const double* E,
+                       const double* S, const double* x, double* y, int32_t nrhs, int32_t ld,
+                       void* stream);
 
 /* Block until the object's work is done and report any device-side failure
  * (HSS_ERR_NOT_SPD ...). */

@@ -401,6 +401,7 @@ const char* hss_strerror(int code) {
     case HSS_ERR_OOM: return "out of device memory";
     case HSS_ERR_TIMEOUT: return "device wait timed out";
     case HSS_ERR_NO_CONVERGENCE: return "iterative refinement did not converge";
+    case HSS_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of hss_matvec_noalloc";
     default: return "unknown error";
   }
 }

@@ -19,7 +19,7 @@ HSS_FP64, HSS_MIXED_TF32, HSS_MIXED_BF16, HSS_MIXED_FP32 = 0, 1, 2, 3
 PRECISIONS = {"fp64": HSS_FP64, "tf32": HSS_MIXED_TF32, "bf16": HSS_MIXED_BF16,
               "fp32": HSS_MIXED_FP32}
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOT_FACTORIZED", -3: "NOT_SPD", -4: "CUDA",
-          -5: "OOM", -6: "TIMEOUT", -7: "NO_CONVERGENCE"}
+          -5: "OOM", -6: "TIMEOUT", -7: "NO_CONVERGENCE", -8: "TOO_LARGE"}
 
 # every entry point declared in include/hss.h: name -> (restype, argtypes)
 _c_int, _c_double, _p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -49,6 +49,8 @@ SIGNATURES = {
     "hss_trace_read": (_c_int, [_p, ctypes.c_int32, ctypes.POINTER(_c_double),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_double)]),
     "hss_launch_count": (_c_int, [_p, ctypes.POINTER(ctypes.c_int64)]),
+    "hss_matvec_noalloc": (_c_int, [ctypes.POINTER(Shape), _p, _p, _p, _p, _p, _p, ctypes.c_int32,
+                                    ctypes.c_int32, _p]),
     "hss_destroy": (None, [_p]),
     "hss_strerror": (ctypes.c_char_p, [_c_int]),
 }
@@ -229,3 +231,29 @@ class HSS:
         _check(load().hss_export(self._h, kinds[what], level, buf.ctypes.data, buf.size),
                "hss_export")
         return buf.reshape(nodes, cols, rows).transpose(0, 2, 1).copy()
+
+
+def packed_generators(h):
+    """(D, U, E, S) of an HSS matrix as flat float64 host arrays in the packed
+    column-major layout of hss_create."""
+    L = h.levels
+    D = _colmajor_blocks(h.D).ravel()
+    U = _colmajor_blocks(h.U).ravel()
+    E = (np.concatenate([_colmajor_blocks(h.E[l]).ravel() for l in range(1, L)])
+         if L >= 2 else np.zeros(1))
+    S = np.concatenate([_colmajor_blocks(h.S[l]).ravel() for l in range(1, L + 1)])
+    return D, U, E, S
+
+
+def matvec_noalloc(shape, D, U, E, S, x, y, stream=None):
+    """y = A x through hss_matvec_noalloc.  D, U, E, S, x, y are CUDA tensors the
+    caller owns (packed layout, see packed_generators); nothing is allocated."""
+    xp, nrhs, ld = _mat_args(x)
+    yp, nrhs2, ld2 = _mat_args(y)
+    if nrhs != nrhs2 or ld != ld2:
+        raise ValueError("x and y need the same shape and leading dimension")
+    sh = Shape(*shape)
+    _check(load().hss_matvec_noalloc(ctypes.byref(sh), D.data_ptr(), U.data_ptr(), E.data_ptr(),
+                                     S.data_ptr(), xp, yp, nrhs, ld, _stream_ptr(stream)),
+           "hss_matvec_noalloc")
+    return y
