@@ -58,7 +58,11 @@ typedef struct hss_s* hss_t;
 /* Arithmetic of the factorization.  HSS_FP64 computes every step in FP64.
  * The mixed modes compute the per-level steps (Alg. 2 lines 2-4) in lower
  * precision and use the factor as the preconditioner of FP64 iterative
- * refinement in hss_solve; the root Cholesky, residual and update are FP64. */
+ * refinement in hss_solve; the root Cholesky, residual and update are FP64.
+ * HSS_MIXED_FP32: every per-level step in FP32 (FP32 accumulation).
+ * HSS_MIXED_TF32 / HSS_MIXED_BF16: the dense contractions of the diagonal
+ * product on tensor cores; hss_factorize returns HSS_ERR_INVALID_ARG for a
+ * mode this build does not provide. */
 typedef enum {
   HSS_FP64 = 0,
   HSS_MIXED_TF32 = 1,
@@ -112,8 +116,9 @@ int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, voi
 
 /* log det A from the factorized form (Eq. hss-ulv-final-form): twice the sum of
  * the logs of the diagonals of every L^RR and of the root factor.  Writes one
- * host double.  Synchronizes the object's last stream.  Errors: NOT_FACTORIZED,
- * NOT_SPD. */
+ * host double.  For a mixed factor it is the log-determinant of that
+ * lower-precision factor (root in FP64), not refined.  Synchronizes the
+ * object's last stream.  Errors: NOT_FACTORIZED, NOT_SPD. */
 int hss_logdet(hss_t h, double* out);
 
 /* y = A x with the HSS generators (the product A·b of the construction-error
@@ -180,8 +185,9 @@ typedef enum {
   HSS_K_PCHOL = 4,     /* partial Cholesky + merge epilogue, root Cholesky */
   HSS_K_TRSV_FWD = 5,  /* forward triangular sweep of the solve */
   HSS_K_TRSV_BWD = 6,  /* backward triangular sweep of the solve */
-  HSS_K_OTHER = 7,     /* log-det reduction and small helpers */
-  HSS_K_COUNT = 8
+  HSS_K_OTHER = 7,     /* log-det reduction, precision conversion, refinement helpers */
+  HSS_K_COUNT = 8,
+  HSS_K_FP32 = 8       /* added to a class: the same kernel run in FP32 (mixed modes) */
 } hss_kernel_kind;
 
 /* Per-kernel timing: with enable = 1 every later launch of the object is
@@ -190,8 +196,9 @@ typedef enum {
  * instructions); enable = 0 stops logging.  Enabling clears the log. */
 int hss_trace(hss_t h, int32_t enable);
 
-/* Sum of the logged launches of one kernel class: total device milliseconds,
- * number of launches and algorithmic flops.  Synchronizes the logged streams.
+/* Sum of the logged launches of one kernel class (0 .. 2*HSS_K_COUNT-1; classes
+ * from HSS_K_FP32 on are the FP32 launches): total device milliseconds, number
+ * of launches and algorithmic flops.  Synchronizes the logged streams.
  * Errors: INVALID_ARG. */
 int hss_trace_read(hss_t h, int32_t kind, double* ms, int64_t* launches, double* flops);
 

@@ -1,9 +1,12 @@
-// C ABI of the HSS-ULV library: the device-resident object, its arena, and the
-// level schedule of Alg. 2 (factor), the solve of Sec. 3.2 and the HSS matvec.
+// C ABI of the HSS-ULV library: the device-resident object, its arenas, and the
+// level schedule of Alg. 2 (factor), the solve of Sec. 3.2, the HSS matvec and
+// iterative refinement for the mixed-precision factor.
 //
 // Per level l the work is batched over the 2^l nodes of the level; each step is
 // one launch (batched GEMM / SYR2K / per-node kernel), so a level costs a fixed
-// handful of launches whatever its node count.
+// handful of launches whatever its node count.  The schedule is written once,
+// templated on the arithmetic type: double for HSS_FP64, float for the mixed
+// modes (whose root Cholesky, residual and update stay in double).
 #include <math.h>
 #include <string.h>
 
@@ -13,24 +16,35 @@
 
 #include "../../include/hss.h"
 #include "common.cuh"
+#include "ir_kernels.cuh"
 #include "ulv_kernels.cuh"
 
 namespace {
 
 constexpr int kMaxCols = 32;      // right-hand-side columns per matvec pass
-constexpr int kSolveCols = 16;    // columns per triangular-sweep pass
+constexpr int kSolveCols = 16;    // columns per triangular-sweep / refinement pass
 
-struct Level {
+template <typename T>
+struct LevelT {
   int n = 0, b = 0, r = 0, c = 0;
-  double* V = nullptr;   // n x b x r
-  double* T = nullptr;   // n x r x r
-  double* LB = nullptr;  // n x r x r
-  double* M = nullptr;   // n x b x b factored blocks (leaves: own buffer; else = A)
-  double* A = nullptr;   // n x b x b merged blocks (levels < L), 1 block at the root
-  double* B = nullptr;   // n x b x r bases fed to the QL (levels 1 .. L-1)
-  double* yv = nullptr;  // level vector for the solve: (n b) x kSolveCols
-  double* xh = nullptr;  // matvec up-sweep: (n r) x kMaxCols
-  double* yh = nullptr;  // matvec down-sweep: (n r) x kMaxCols
+  T* V = nullptr;   // n x b x r Householder vectors
+  T* T_ = nullptr;  // n x r x r compact-WY factor
+  T* LB = nullptr;  // n x r x r, L_B = Q^Sᵀ B
+  T* M = nullptr;   // n x b x b factored blocks (leaves: own buffer; else = A)
+  T* A = nullptr;   // n x b x b merged blocks (levels < L), 1 block at the root
+  T* B = nullptr;   // n x b x r bases fed to the QL (levels 1 .. L-1)
+  T* yv = nullptr;  // level vector of the solve: (n b) x kSolveCols
+};
+
+template <typename T>
+struct Factor {
+  std::vector<LevelT<T>> lv;   // index = level (0 = root)
+  T *W = nullptr, *Y = nullptr, *X = nullptr, *Z = nullptr, *t1 = nullptr, *t2 = nullptr;
+  const T *D = nullptr, *U = nullptr, *E = nullptr, *S = nullptr;   // generators in T
+  T *Dc = nullptr, *Uc = nullptr, *Ec = nullptr, *Sc = nullptr;     // converted copies (float)
+  T* d = nullptr;               // n x kSolveCols refinement correction (float)
+  void* arena = nullptr;
+  size_t bytes = 0;
 };
 
 }  // namespace
@@ -39,11 +53,16 @@ struct hss_s {
   int n = 0, leaf = 0, rank = 0, L = 0;
   int device = 0;
   double *D = nullptr, *U = nullptr, *E = nullptr, *S = nullptr;
+  long long esz = 0, ssz = 0;
   std::vector<long long> Eoff, Soff;   // element offset of level l in E / S
-  std::vector<Level> lv;               // index = level (0 = root)
-  double *W = nullptr, *Y = nullptr;   // n_L x b x r scratch
-  double *X = nullptr, *Z = nullptr;   // n_L x r x r scratch
-  double *t1 = nullptr, *t2 = nullptr; // n_L x r x kMaxCols scratch
+  Factor<double> f64;
+  Factor<float> f32;
+  std::vector<double*> xh, yh;         // matvec up / down sweep per level: (2^l r) x kMaxCols
+  double* R0 = nullptr;                // FP64 root block of a mixed factor (2r x 2r)
+  double* root_vec = nullptr;          // FP64 root vector of a mixed solve (2r x kSolveCols)
+  double* rbuf = nullptr;              // n x kSolveCols residual
+  double* bbuf = nullptr;              // n x kSolveCols copy of b (x aliasing b)
+  double* norms = nullptr;             // 4 x kSolveCols: |b|, 1/|b|, |r|, 1/|r|
   double* logdet_part = nullptr;       // 2^(L+1) - 1 node contributions
   double* logdet_val = nullptr;
   int* status = nullptr;
@@ -51,6 +70,8 @@ struct hss_s {
   size_t arena_bytes = 0;
   int factorized = 0;
   int precision = HSS_FP64;
+  int ir_max_it = 30;
+  double ir_tol = 1e-12;
   cudaStream_t last_stream = nullptr;
   int ir_iters = 0;
   double ir_resid = 0.0;
@@ -70,74 +91,114 @@ namespace {
 struct Bump {
   char* base;
   size_t off = 0;
-  size_t cap;
   template <typename T>
   T* take(size_t count) {
     off = (off + 255) & ~size_t(255);
-    T* p = reinterpret_cast<T*>(base + off);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
     off += count * sizeof(T);
     return p;
   }
 };
 
-// lays the object out in [base, base + cap); with base = nullptr only measures
-size_t layout(hss_s* h, char* base) {
-  Bump bp{base, 0, 0};
-  const int L = h->L, r = h->rank, leaf = h->leaf;
-  const long long nL = 1LL << L;
-  h->D = bp.take<double>(nL * leaf * leaf);
-  h->U = bp.take<double>(nL * leaf * r);
-  long long esz = 0, ssz = 0;
-  h->Eoff.assign(L + 1, 0);
-  h->Soff.assign(L + 1, 0);
-  for (int l = 1; l <= L - 1; ++l) {
-    h->Eoff[l] = esz;
-    esz += (1LL << l) * 2 * r * r;
-  }
-  for (int l = 1; l <= L; ++l) {
-    h->Soff[l] = ssz;
-    ssz += (1LL << (l - 1)) * r * r;
-  }
-  h->E = bp.take<double>(std::max<long long>(esz, 1));
-  h->S = bp.take<double>(ssz);
-  h->lv.assign(L + 1, Level());
+template <typename T>
+void layout_factor(Bump& bp, Factor<T>& f, int L, int leaf, int r) {
+  f.lv.assign(L + 1, LevelT<T>());
+  const size_t nL = size_t(1) << L;
   for (int l = 0; l <= L; ++l) {
-    Level& P = h->lv[l];
+    LevelT<T>& P = f.lv[l];
     P.n = 1 << l;
     P.b = (l == L) ? leaf : 2 * r;
     P.r = (l == 0) ? 0 : r;
     P.c = P.b - P.r;
     if (l >= 1) {
-      P.V = bp.take<double>((size_t)P.n * P.b * r);
-      P.T = bp.take<double>((size_t)P.n * r * r);
-      P.LB = bp.take<double>((size_t)P.n * r * r);
+      P.V = bp.take<T>((size_t)P.n * P.b * r);
+      P.T_ = bp.take<T>((size_t)P.n * r * r);
+      P.LB = bp.take<T>((size_t)P.n * r * r);
     }
     if (l < L) {
-      P.A = bp.take<double>((size_t)P.n * P.b * P.b);
+      P.A = bp.take<T>((size_t)P.n * P.b * P.b);
       P.M = P.A;
     } else {
-      P.M = bp.take<double>((size_t)P.n * P.b * P.b);
+      P.M = bp.take<T>((size_t)P.n * P.b * P.b);
     }
-    if (l >= 1 && l < L) P.B = bp.take<double>((size_t)P.n * P.b * r);
-    if (l < L) P.yv = bp.take<double>((size_t)P.n * P.b * kSolveCols);
-    if (l >= 1) {
-      P.xh = bp.take<double>((size_t)P.n * r * kMaxCols);
-      P.yh = bp.take<double>((size_t)P.n * r * kMaxCols);
-    }
+    if (l >= 1 && l < L) P.B = bp.take<T>((size_t)P.n * P.b * r);
+    if (l < L) P.yv = bp.take<T>((size_t)P.n * P.b * kSolveCols);
   }
-  h->W = bp.take<double>((size_t)nL * leaf * r);
-  h->Y = bp.take<double>((size_t)nL * leaf * r);
-  h->X = bp.take<double>((size_t)nL * r * r);
-  h->Z = bp.take<double>((size_t)nL * r * r);
-  h->t1 = bp.take<double>((size_t)nL * r * kMaxCols);
-  h->t2 = bp.take<double>((size_t)nL * r * kMaxCols);
+  f.W = bp.take<T>(nL * leaf * r);
+  f.Y = bp.take<T>(nL * leaf * r);
+  f.X = bp.take<T>(nL * r * r);
+  f.Z = bp.take<T>(nL * r * r);
+  f.t1 = bp.take<T>(nL * r * kMaxCols);
+  f.t2 = bp.take<T>(nL * r * kMaxCols);
+}
+
+// the object's main arena: FP64 generators, FP64 factor, matvec and refinement
+size_t layout_main(hss_s* h, char* base) {
+  Bump bp{base};
+  const int L = h->L, r = h->rank, leaf = h->leaf;
+  const long long nL = 1LL << L;
+  h->D = bp.take<double>(nL * leaf * leaf);
+  h->U = bp.take<double>(nL * leaf * r);
+  h->Eoff.assign(L + 1, 0);
+  h->Soff.assign(L + 1, 0);
+  h->esz = h->ssz = 0;
+  for (int l = 1; l <= L - 1; ++l) {
+    h->Eoff[l] = h->esz;
+    h->esz += (1LL << l) * 2 * r * r;
+  }
+  for (int l = 1; l <= L; ++l) {
+    h->Soff[l] = h->ssz;
+    h->ssz += (1LL << (l - 1)) * r * r;
+  }
+  h->E = bp.take<double>(std::max<long long>(h->esz, 1));
+  h->S = bp.take<double>(h->ssz);
+  layout_factor<double>(bp, h->f64, L, leaf, r);
+  h->f64.D = h->D;
+  h->f64.U = h->U;
+  h->f64.E = h->E;
+  h->f64.S = h->S;
+  h->xh.assign(L + 1, nullptr);
+  h->yh.assign(L + 1, nullptr);
+  for (int l = 1; l <= L; ++l) {
+    h->xh[l] = bp.take<double>((size_t(1) << l) * r * kMaxCols);
+    h->yh[l] = bp.take<double>((size_t(1) << l) * r * kMaxCols);
+  }
+  h->R0 = bp.take<double>((size_t)4 * r * r);
+  h->root_vec = bp.take<double>((size_t)2 * r * kSolveCols);
+  h->rbuf = bp.take<double>((size_t)h->n * kSolveCols);
+  h->bbuf = bp.take<double>((size_t)h->n * kSolveCols);
+  h->norms = bp.take<double>(4 * kSolveCols);
   h->logdet_part = bp.take<double>((size_t)(2 * nL - 1));
   h->logdet_val = bp.take<double>(1);
   h->status = bp.take<int>(8);
   return bp.off + 256;
 }
 
+// the FP32 arena of the mixed modes: converted generators, factor, correction
+size_t layout_f32(hss_s* h, char* base) {
+  Bump bp{base};
+  const int L = h->L, r = h->rank, leaf = h->leaf;
+  const long long nL = 1LL << L;
+  Factor<float>& f = h->f32;
+  f.Dc = bp.take<float>(nL * leaf * leaf);
+  f.Uc = bp.take<float>(nL * leaf * r);
+  f.Ec = bp.take<float>(std::max<long long>(h->esz, 1));
+  f.Sc = bp.take<float>(h->ssz);
+  layout_factor<float>(bp, f, L, leaf, r);
+  f.d = bp.take<float>((size_t)h->n * kSolveCols);
+  f.D = f.Dc;
+  f.U = f.Uc;
+  f.E = f.Ec;
+  f.S = f.Sc;
+  return bp.off + 256;
+}
+
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? HSS_OK : HSS_ERR_CUDA; }
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HSS_OK : HSS_ERR_CUDA;
+}
 
 // Brackets one kernel launch: counts it and, when tracing, logs two events.
 struct Launch {
@@ -145,8 +206,10 @@ struct Launch {
   cudaStream_t st;
   hss_s::Rec rec{};
   bool on = false;
-  Launch(hss_s* h_, int kind, double flops, cudaStream_t st_) : h(h_), st(st_) {
+  Launch(hss_s* h_, int kind, double flops, cudaStream_t st_, bool f32 = false)
+      : h(h_), st(st_) {
     ++h->launches;
+    if (f32) kind += HSS_K_FP32;
     if (h->tracing) {
       rec.kind = kind;
       rec.flops = flops;
@@ -172,20 +235,14 @@ void clear_trace(hss_s* h) {
   h->trace.clear();
 }
 
-double gemm_flops(int m, int n, int k, int batch) { return 2.0 * m * n * (double)k * batch; }
-
-void gemm(hss_s* h, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
-          long long sA, const double* B, int ldb, long long sB, double beta, double* C, int ldc,
-          long long sC, int batch, cudaStream_t st) {
+template <typename T>
+void gemm(hss_s* h, bool ta, bool tb, int m, int n, int k, T alpha, const T* A, int lda,
+          long long sA, const T* B, int ldb, long long sB, T beta, T* C, int ldc, long long sC,
+          int batch, cudaStream_t st) {
   if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return;
-  Launch l(h, n <= 32 ? HSS_K_GEMM_SKINNY : HSS_K_GEMM, gemm_flops(m, n, k, batch), st);
-  gemm_batched<double>(ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
-                       st);
-}
-
-int check_launch() {
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? HSS_OK : HSS_ERR_CUDA;
+  Launch l(h, n <= 32 ? HSS_K_GEMM_SKINNY : HSS_K_GEMM, 2.0 * m * n * (double)k * batch, st,
+           sizeof(T) == 4);
+  gemm_batched<T>(ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, st);
 }
 
 // partial Cholesky of the first c of b columns: POTRF c x c, TRSM (b-c) x c,
@@ -196,90 +253,122 @@ double pchol_flops(int b, int c) {
 }
 
 // triangular sweep of one node: c x c triangle plus the (b-c) x c block
-double trsv_flops(int b, int c, int nrhs) {
-  return ((double)c * c + 2.0 * (b - c) * c) * nrhs;
-}
+double trsv_flops(int b, int c, int nrhs) { return ((double)c * c + 2.0 * (b - c) * c) * nrhs; }
 
-// Q application on a level vector: vec_seg := vec_seg - V op(T) (Vᵀ vec_seg)
-// (op(T) = Tᵀ for Qᵀ, T for Q), nc <= kMaxCols columns
-void apply_q(hss_s* h, const Level& P, double* vec, int ldv, int nc, bool transpose,
+// vec_seg := vec_seg - V op(T) (Vᵀ vec_seg), op(T) = Tᵀ for Qᵀ and T for Q
+template <typename T>
+void apply_q(hss_s* h, Factor<T>& f, const LevelT<T>& P, T* vec, int ldv, int nc, bool transpose,
              cudaStream_t st) {
   const int b = P.b, r = P.r, n = P.n;
   const long long s1 = (long long)r * kMaxCols;
-  gemm(h, true, false, r, nc, b, 1.0, P.V, b, (long long)b * r, vec, ldv, b, 0.0,
-                       h->t1, r, s1, n, st);
-  gemm(h, transpose, false, r, nc, r, 1.0, P.T, r, (long long)r * r, h->t1, r, s1,
-                       0.0, h->t2, r, s1, n, st);
-  gemm(h, false, false, b, nc, r, -1.0, P.V, b, (long long)b * r, h->t2, r, s1, 1.0,
-                       vec, ldv, b, n, st);
+  gemm<T>(h, true, false, r, nc, b, T(1), P.V, b, (long long)b * r, vec, ldv, b, T(0), f.t1, r, s1,
+          n, st);
+  gemm<T>(h, transpose, false, r, nc, r, T(1), P.T_, r, (long long)r * r, f.t1, r, s1, T(0), f.t2,
+          r, s1, n, st);
+  gemm<T>(h, false, false, b, nc, r, T(-1), P.V, b, (long long)b * r, f.t2, r, s1, T(1), vec, ldv,
+          b, n, st);
 }
 
-int factorize_fp64(hss_s* h, cudaStream_t st) {
+// levels L .. 1 of Alg. 2; leaves the merged root block in f.lv[0].A
+template <typename T>
+int factor_levels(hss_s* h, Factor<T>& f, cudaStream_t st) {
   const int L = h->L, r = h->rank;
   const long long rr = (long long)r * r;
-  cudaMemsetAsync(h->status, 0, 8 * sizeof(int), st);
   for (int l = L; l >= 1; --l) {
-    Level& P = h->lv[l];
-    Level& Q = h->lv[l - 1];
+    LevelT<T>& P = f.lv[l];
+    LevelT<T>& Q = f.lv[l - 1];
     const int b = P.b, n = P.n, c = P.c;
     const long long br = (long long)b * r, bb = (long long)b * b;
     // (a) basis completion (Eq. 2-3)
-    const double* Bsrc = (l == L) ? h->U : P.B;
+    const T* Bsrc = (l == L) ? f.U : P.B;
     {
-      Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, st);
-      launch_ql_basis<double>(Bsrc, b, br, P.V, br, P.T, rr, P.LB, rr, b, r, n, st);
+      Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, st,
+               sizeof(T) == 4);
+      launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, st);
     }
-    // (d, first half) merge: rescaled coupling Ŝ = L_B(c2) S L_B(c1)ᵀ into the
-    // parent's off-diagonal blocks, parent basis blkdiag(L_B(c1), L_B(c2)) E_p
+    // (d, first half) merge: Ŝ = L_B(c2) S L_B(c1)ᵀ and Ŝᵀ into the parent's
+    // off-diagonal blocks, parent basis blkdiag(L_B(c1), L_B(c2)) E_p
     const int np = n / 2;
-    const double* Sl = h->S + h->Soff[l];
+    const T* Sl = f.S + h->Soff[l];
     const int ldq = 2 * r;
     const long long sq = 4 * rr;
-    gemm(h, false, false, r, r, r, 1.0, P.LB + rr, r, 2 * rr, Sl, r, rr, 0.0, h->Z, r,
-                         rr, np, st);
-    gemm(h, false, true, r, r, r, 1.0, h->Z, r, rr, P.LB, r, 2 * rr, 0.0, Q.A + r, ldq,
-                         sq, np, st);
-    gemm(h, false, true, r, r, r, 1.0, P.LB, r, 2 * rr, h->Z, r, rr, 0.0,
-                         Q.A + (long long)r * ldq, ldq, sq, np, st);
+    gemm<T>(h, false, false, r, r, r, T(1), P.LB + rr, r, 2 * rr, Sl, r, rr, T(0), f.Z, r, rr, np,
+            st);
+    gemm<T>(h, false, true, r, r, r, T(1), f.Z, r, rr, P.LB, r, 2 * rr, T(0), Q.A + r, ldq, sq, np,
+            st);
+    gemm<T>(h, false, true, r, r, r, T(1), P.LB, r, 2 * rr, f.Z, r, rr, T(0),
+            Q.A + (long long)r * ldq, ldq, sq, np, st);
     if (l - 1 >= 1) {
-      const double* Ep = h->E + h->Eoff[l - 1];
-      gemm(h, false, false, r, r, r, 1.0, P.LB, r, 2 * rr, Ep, 2 * r, 2 * rr, 0.0,
-                           Q.B, 2 * r, 2 * rr, np, st);
-      gemm(h, false, false, r, r, r, 1.0, P.LB + rr, r, 2 * rr, Ep + r, 2 * r, 2 * rr,
-                           0.0, Q.B + r, 2 * r, 2 * rr, np, st);
+      const T* Ep = f.E + h->Eoff[l - 1];
+      gemm<T>(h, false, false, r, r, r, T(1), P.LB, r, 2 * rr, Ep, 2 * r, 2 * rr, T(0), Q.B, 2 * r,
+              2 * rr, np, st);
+      gemm<T>(h, false, false, r, r, r, T(1), P.LB + rr, r, 2 * rr, Ep + r, 2 * r, 2 * rr, T(0),
+              Q.B + r, 2 * r, 2 * rr, np, st);
     }
     // (b) diagonal product Â = Qᵀ A Q with Q = I - V T Vᵀ, in the symmetric
     // compact-WY form Â = A - Y'Vᵀ - V Y'ᵀ, Y' = A V T - ½ V Tᵀ Vᵀ A V T
-    const double* Ain = (l == L) ? h->D : P.A;
-    gemm(h, false, false, b, r, b, 1.0, Ain, b, bb, P.V, b, br, 0.0, h->W, b, br, n,
-                         st);
-    gemm(h, false, false, b, r, r, 1.0, h->W, b, br, P.T, r, rr, 0.0, h->Y, b, br, n,
-                         st);
-    gemm(h, true, false, r, r, b, 1.0, P.V, b, br, h->Y, b, br, 0.0, h->X, r, rr, n,
-                         st);
-    gemm(h, true, false, r, r, r, 1.0, P.T, r, rr, h->X, r, rr, 0.0, h->Z, r, rr, n,
-                         st);
-    gemm(h, false, false, b, r, r, -0.5, P.V, b, br, h->Z, r, rr, 1.0, h->Y, b, br, n,
-                         st);
+    const T* Ain = (l == L) ? f.D : P.A;
+    gemm<T>(h, false, false, b, r, b, T(1), Ain, b, bb, P.V, b, br, T(0), f.W, b, br, n, st);
+    gemm<T>(h, false, false, b, r, r, T(1), f.W, b, br, P.T_, r, rr, T(0), f.Y, b, br, n, st);
+    gemm<T>(h, true, false, r, r, b, T(1), P.V, b, br, f.Y, b, br, T(0), f.X, r, rr, n, st);
+    gemm<T>(h, true, false, r, r, r, T(1), P.T_, r, rr, f.X, r, rr, T(0), f.Z, r, rr, n, st);
+    gemm<T>(h, false, false, b, r, r, T(-0.5), P.V, b, br, f.Z, r, rr, T(1), f.Y, b, br, n, st);
     {
-      Launch k(h, HSS_K_SYR2K, 2.0 * r * b * (b + 1.0) * n, st);
-      syr2k_lower_batched<double>(b, r, Ain, b, bb, h->Y, b, br, P.V, b, br, P.M, b, bb, n, st);
+      Launch k(h, HSS_K_SYR2K, 2.0 * r * b * (b + 1.0) * n, st, sizeof(T) == 4);
+      syr2k_lower_batched<T>(b, r, Ain, b, bb, f.Y, b, br, P.V, b, br, P.M, b, bb, n, st);
     }
     // (c) partial Cholesky + (d, second half) Schur complements into the parent
     {
-      Launch k(h, HSS_K_PCHOL, pchol_flops(b, c) * n, st);
-      launch_pchol<double>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1), l,
-                           0, h->status, n, st);
+      Launch k(h, HSS_K_PCHOL, pchol_flops(b, c) * n, st, sizeof(T) == 4);
+      launch_pchol<T>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1), l, 0,
+                      h->status, n, st);
     }
     int rc = check_launch();
     if (rc) return rc;
   }
-  // root Cholesky (Alg. 2 line 6)
-  Level& R0 = h->lv[0];
+  return HSS_OK;
+}
+
+int factorize(hss_s* h, int prec, cudaStream_t st) {
+  const int L = h->L, r = h->rank;
+  cudaMemsetAsync(h->status, 0, 8 * sizeof(int), st);
+  double* root = nullptr;
+  if (prec == HSS_FP64) {
+    int rc = factor_levels<double>(h, h->f64, st);
+    if (rc) return rc;
+    root = h->f64.lv[0].A;
+  } else {
+    Factor<float>& f = h->f32;
+    {   // the generators in FP32 (part of every factorization)
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_f64_to_f32(h->D, f.Dc, (1LL << L) * h->leaf * h->leaf, st);
+    }
+    {
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_f64_to_f32(h->U, f.Uc, (1LL << L) * h->leaf * r, st);
+    }
+    if (h->esz) {
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_f64_to_f32(h->E, f.Ec, h->esz, st);
+    }
+    {
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_f64_to_f32(h->S, f.Sc, h->ssz, st);
+    }
+    int rc = factor_levels<float>(h, f, st);
+    if (rc) return rc;
+    {   // the root block goes to FP64 for the root Cholesky
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_f32_to_f64(f.lv[0].A, h->R0, 4LL * r * r, st);
+    }
+    root = h->R0;
+  }
+  // root Cholesky (Alg. 2 line 6), FP64 in every mode
+  const int b0 = 2 * r;
   {
-    Launch k(h, HSS_K_PCHOL, pchol_flops(R0.b, R0.b), st);
-    launch_pchol<double>(R0.A, R0.b, (long long)R0.b * R0.b, R0.b, R0.b, nullptr, 0, 0,
-                         h->logdet_part, 0, 0, h->status, 1, st);
+    Launch k(h, HSS_K_PCHOL, pchol_flops(b0, b0), st);
+    launch_pchol<double>(root, b0, (long long)b0 * b0, b0, b0, nullptr, 0, 0, h->logdet_part, 0,
+                         0, h->status, 1, st);
   }
   {
     Launch k(h, HSS_K_OTHER, (double)((2LL << L) - 1), st);
@@ -288,93 +377,93 @@ int factorize_fp64(hss_s* h, cudaStream_t st) {
   return check_launch();
 }
 
-int solve_fp64(hss_s* h, double* x, int nrhs, int ld, cudaStream_t st) {
+// the ULV sweeps on nc <= kSolveCols columns of x (in place), arithmetic T;
+// the root solve is FP64 in every mode
+template <typename T>
+int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) {
   const int L = h->L, r = h->rank;
-  for (int j0 = 0; j0 < nrhs; j0 += kSolveCols) {
-    const int nc = std::min(kSolveCols, nrhs - j0);
-    double* xc = x + (long long)j0 * ld;
-    // forward sweep, leaves -> root
-    for (int l = L; l >= 1; --l) {
-      Level& P = h->lv[l];
-      Level& Q = h->lv[l - 1];
-      double* vec = (l == L) ? xc : P.yv;
-      const int ldv = (l == L) ? ld : P.n * P.b;
-      apply_q(h, P, vec, ldv, nc, /*transpose=*/true, st);
-      {
-        Launch k(h, HSS_K_TRSV_FWD, trsv_flops(P.b, P.c, nc) * P.n, st);
-        launch_trsv_fwd<double>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                                Q.n * Q.b, r, P.n, st);
-      }
-    }
-    Level& R0 = h->lv[0];
-    {
-      Launch k(h, HSS_K_TRSV_FWD, trsv_flops(R0.b, R0.b, nc), st);
-      launch_trsv_fwd<double>(R0.A, R0.b, 0, R0.b, R0.b, R0.yv, R0.b, 0, nc, nullptr, 0, 0, 1,
-                              st);
-    }
-    {
-      Launch k(h, HSS_K_TRSV_BWD, trsv_flops(R0.b, R0.b, nc), st);
-      launch_trsv_bwd<double>(R0.A, R0.b, 0, R0.b, R0.b, R0.yv, R0.b, 0, nc, nullptr, 0, 0, 1,
-                              st);
-    }
-    // backward sweep, root -> leaves
-    for (int l = 1; l <= L; ++l) {
-      Level& P = h->lv[l];
-      Level& Q = h->lv[l - 1];
-      double* vec = (l == L) ? xc : P.yv;
-      const int ldv = (l == L) ? ld : P.n * P.b;
-      {
-        Launch k(h, HSS_K_TRSV_BWD, trsv_flops(P.b, P.c, nc) * P.n, st);
-        launch_trsv_bwd<double>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                                Q.n * Q.b, r, P.n, st);
-      }
-      apply_q(h, P, vec, ldv, nc, /*transpose=*/false, st);
-    }
-    int rc = check_launch();
-    if (rc) return rc;
+  for (int l = L; l >= 1; --l) {
+    LevelT<T>& P = f.lv[l];
+    LevelT<T>& Q = f.lv[l - 1];
+    T* vec = (l == L) ? x : P.yv;
+    const int ldv = (l == L) ? ld : P.n * P.b;
+    apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/true, st);
+    Launch k(h, HSS_K_TRSV_FWD, trsv_flops(P.b, P.c, nc) * P.n, st, sizeof(T) == 4);
+    launch_trsv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                       Q.n * Q.b, r, P.n, st);
   }
-  return HSS_OK;
+  const int b0 = 2 * r;
+  double* rootA;
+  double* rv;
+  if (sizeof(T) == sizeof(double)) {
+    rootA = reinterpret_cast<double*>(f.lv[0].A);
+    rv = reinterpret_cast<double*>(f.lv[0].yv);
+  } else {
+    rootA = h->R0;
+    rv = h->root_vec;
+    Launch k(h, HSS_K_OTHER, 0.0, st);
+    launch_f32_to_f64(reinterpret_cast<const float*>(f.lv[0].yv), rv, (long long)b0 * nc, st);
+  }
+  {
+    Launch k(h, HSS_K_TRSV_FWD, trsv_flops(b0, b0, nc), st);
+    launch_trsv_fwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st);
+  }
+  {
+    Launch k(h, HSS_K_TRSV_BWD, trsv_flops(b0, b0, nc), st);
+    launch_trsv_bwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st);
+  }
+  if (sizeof(T) != sizeof(double)) {
+    Launch k(h, HSS_K_OTHER, 0.0, st);
+    launch_f64_to_f32(rv, reinterpret_cast<float*>(f.lv[0].yv), (long long)b0 * nc, st);
+  }
+  for (int l = 1; l <= L; ++l) {
+    LevelT<T>& P = f.lv[l];
+    LevelT<T>& Q = f.lv[l - 1];
+    T* vec = (l == L) ? x : P.yv;
+    const int ldv = (l == L) ? ld : P.n * P.b;
+    {
+      Launch k(h, HSS_K_TRSV_BWD, trsv_flops(P.b, P.c, nc) * P.n, st, sizeof(T) == 4);
+      launch_trsv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                         Q.n * Q.b, r, P.n, st);
+    }
+    apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/false, st);
+  }
+  return check_launch();
 }
 
-int matvec_fp64(hss_s* h, const double* x, double* y, int nrhs, int ld, cudaStream_t st) {
+int matvec_fp64(hss_s* h, const double* x, int ldx, double* y, int ldy, int nrhs,
+                cudaStream_t st) {
   const int L = h->L, r = h->rank, leaf = h->leaf;
   const long long rr = (long long)r * r;
   const int nL = 1 << L;
   for (int j0 = 0; j0 < nrhs; j0 += kMaxCols) {
     const int nc = std::min(kMaxCols, nrhs - j0);
-    const double* xc = x + (long long)j0 * ld;
-    double* yc = y + (long long)j0 * ld;
+    const double* xc = x + (long long)j0 * ldx;
+    double* yc = y + (long long)j0 * ldy;
     // up-sweep: x̂_L = Uᵀ x, x̂_l = E_lᵀ [x̂_{l+1}(2p); x̂_{l+1}(2p+1)]
-    gemm(h, true, false, r, nc, leaf, 1.0, h->U, leaf, (long long)leaf * r, xc, ld,
-                         leaf, 0.0, h->lv[L].xh, nL * r, r, nL, st);
-    for (int l = L - 1; l >= 1; --l) {
-      Level& P = h->lv[l];
-      Level& C = h->lv[l + 1];
-      gemm(h, true, false, r, nc, 2 * r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, C.xh,
-                           C.n * r, 2 * r, 0.0, P.xh, P.n * r, r, P.n, st);
-    }
-    // sibling couplings of every level
+    gemm<double>(h, true, false, r, nc, leaf, 1.0, h->U, leaf, (long long)leaf * r, xc, ldx, leaf,
+                 0.0, h->xh[L], nL * r, r, nL, st);
+    for (int l = L - 1; l >= 1; --l)
+      gemm<double>(h, true, false, r, nc, 2 * r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, h->xh[l + 1],
+                   (2 << l) * r, 2 * r, 0.0, h->xh[l], (1 << l) * r, r, 1 << l, st);
+    // sibling couplings of every level (these initialise ŷ)
     for (int l = 1; l <= L; ++l) {
-      Level& P = h->lv[l];
       const double* Sl = h->S + h->Soff[l];
-      const int ldl = P.n * r;
-      gemm(h, false, false, r, nc, r, 1.0, Sl, r, rr, P.xh, ldl, 2 * r, 0.0, P.yh + r,
-                           ldl, 2 * r, P.n / 2, st);
-      gemm(h, true, false, r, nc, r, 1.0, Sl, r, rr, P.xh + r, ldl, 2 * r, 0.0, P.yh,
-                           ldl, 2 * r, P.n / 2, st);
+      const int ldl = (1 << l) * r;
+      gemm<double>(h, false, false, r, nc, r, 1.0, Sl, r, rr, h->xh[l], ldl, 2 * r, 0.0,
+                   h->yh[l] + r, ldl, 2 * r, 1 << (l - 1), st);
+      gemm<double>(h, true, false, r, nc, r, 1.0, Sl, r, rr, h->xh[l] + r, ldl, 2 * r, 0.0,
+                   h->yh[l], ldl, 2 * r, 1 << (l - 1), st);
     }
     // down-sweep: ŷ_{l+1}(children) += E_l ŷ_l
-    for (int l = 1; l <= L - 1; ++l) {
-      Level& P = h->lv[l];
-      Level& C = h->lv[l + 1];
-      gemm(h, false, false, 2 * r, nc, r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, P.yh,
-                           P.n * r, r, 1.0, C.yh, C.n * r, 2 * r, P.n, st);
-    }
+    for (int l = 1; l <= L - 1; ++l)
+      gemm<double>(h, false, false, 2 * r, nc, r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, h->yh[l],
+                   (1 << l) * r, r, 1.0, h->yh[l + 1], (2 << l) * r, 2 * r, 1 << l, st);
     // leaves: y = D x + U ŷ
-    gemm(h, false, false, leaf, nc, leaf, 1.0, h->D, leaf, (long long)leaf * leaf, xc,
-                         ld, leaf, 0.0, yc, ld, leaf, nL, st);
-    gemm(h, false, false, leaf, nc, r, 1.0, h->U, leaf, (long long)leaf * r,
-                         h->lv[L].yh, nL * r, r, 1.0, yc, ld, leaf, nL, st);
+    gemm<double>(h, false, false, leaf, nc, leaf, 1.0, h->D, leaf, (long long)leaf * leaf, xc, ldx,
+                 leaf, 0.0, yc, ldy, leaf, nL, st);
+    gemm<double>(h, false, false, leaf, nc, r, 1.0, h->U, leaf, (long long)leaf * r, h->yh[L],
+                 nL * r, r, 1.0, yc, ldy, leaf, nL, st);
     int rc = check_launch();
     if (rc) return rc;
   }
@@ -385,6 +474,90 @@ int read_status(hss_s* h, int* st_host) {
   cudaError_t e = cudaMemcpy(st_host, h->status, 8 * sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return HSS_ERR_CUDA;
   return st_host[ST_CODE];
+}
+
+// Iterative refinement with the FP32 factor: x_0 = M⁻¹ b; r_k = b - A x_k in
+// FP64; stop when every column's |r_k| / |b| <= tol; x_{k+1} = x_k + M⁻¹ r_k.
+// Right-hand sides enter the FP32 sweeps scaled to unit norm.
+int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_t st) {
+  const int n = h->n;
+  Factor<float>& f = h->f32;
+  double* nb = h->norms;                    // |b|
+  double* ib = h->norms + kSolveCols;       // 1 / |b|
+  double* nr = h->norms + 2 * kSolveCols;   // |r|
+  double* ir = h->norms + 3 * kSolveCols;   // 1 / |r|
+  int worst_it = 0;
+  double worst_res = 0.0;
+  int result = HSS_OK;
+  for (int j0 = 0; j0 < nrhs; j0 += kSolveCols) {
+    const int nc = std::min(kSolveCols, nrhs - j0);
+    const double* bc = b + (long long)j0 * ld;
+    double* xc = x + (long long)j0 * ld;
+    int ldb = ld;
+    if (bc == xc) {   // keep b: x is overwritten by the iterates
+      if (cudaMemcpy2DAsync(h->bbuf, sizeof(double) * n, bc, sizeof(double) * ld,
+                            sizeof(double) * n, nc, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return HSS_ERR_CUDA;
+      bc = h->bbuf;
+      ldb = n;
+    }
+    {
+      Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
+      launch_col_norms(bc, ldb, n, nc, nb, ib, st);
+    }
+    {
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_cols_to_f32(bc, ldb, f.d, n, n, nc, ib, st);
+    }
+    int rc = solve_sweeps<float>(h, f, f.d, nc, n, st);
+    if (rc) return rc;
+    {
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_cols_update(xc, ld, f.d, n, n, nc, nb, /*accumulate=*/0, st);
+    }
+    double hnb[kSolveCols], hnr[kSolveCols];
+    if (cudaMemcpyAsync(hnb, nb, sizeof(double) * nc, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return HSS_ERR_CUDA;
+    int it = 0;
+    double rel = 0.0;
+    for (;; ++it) {
+      rc = matvec_fp64(h, xc, ld, h->rbuf, n, nc, st);   // rbuf: n x nc, ld = n
+      if (rc) return rc;
+      {
+        Launch k(h, HSS_K_OTHER, (double)n * nc, st);
+        launch_residual(bc, ldb, h->rbuf, n, n, nc, st);
+      }
+      {
+        Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
+        launch_col_norms(h->rbuf, n, n, nc, nr, ir, st);
+      }
+      if (cudaMemcpyAsync(hnr, nr, sizeof(double) * nc, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HSS_ERR_CUDA;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+      int s[8];
+      int code = read_status(h, s);
+      if (code) return code;
+      rel = 0.0;
+      for (int j = 0; j < nc; ++j) rel = std::max(rel, hnb[j] > 0 ? hnr[j] / hnb[j] : hnr[j]);
+      if (!(rel > h->ir_tol) || it >= h->ir_max_it) break;
+      {
+        Launch k(h, HSS_K_OTHER, 0.0, st);
+        launch_cols_to_f32(h->rbuf, n, f.d, n, n, nc, ir, st);
+      }
+      rc = solve_sweeps<float>(h, f, f.d, nc, n, st);
+      if (rc) return rc;
+      {
+        Launch k(h, HSS_K_OTHER, (double)n * nc, st);
+        launch_cols_update(xc, ld, f.d, n, n, nc, nr, /*accumulate=*/1, st);
+      }
+    }
+    worst_it = std::max(worst_it, it);
+    worst_res = std::max(worst_res, rel);
+    if (rel > h->ir_tol || !(rel == rel)) result = HSS_ERR_NO_CONVERGENCE;
+  }
+  h->ir_iters = worst_it;
+  h->ir_resid = worst_res;
+  return result;
 }
 
 }  // namespace
@@ -422,7 +595,7 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   h->rank = r;
   h->L = L;
   cudaGetDevice(&h->device);
-  const size_t bytes = layout(h, nullptr);
+  const size_t bytes = layout_main(h, nullptr);
   void* mem = nullptr;
   if (cudaMalloc(&mem, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -431,18 +604,14 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   }
   h->arena = mem;
   h->arena_bytes = bytes;
-  layout(h, static_cast<char*>(mem));
+  layout_main(h, static_cast<char*>(mem));
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const long long nL = 1LL << L;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemcpy(h->D, D, sizeof(double) * nL * leaf * leaf, kind);
   e = e ? e : cudaMemcpy(h->U, U, sizeof(double) * nL * leaf * r, kind);
-  if (L >= 2) {
-    const long long esz = h->Eoff[L - 1] + (1LL << (L - 1)) * 2 * r * r;
-    e = e ? e : cudaMemcpy(h->E, E, sizeof(double) * esz, kind);
-  }
-  const long long ssz = h->Soff[L] + (1LL << (L - 1)) * (long long)r * r;
-  e = e ? e : cudaMemcpy(h->S, S, sizeof(double) * ssz, kind);
+  if (L >= 2) e = e ? e : cudaMemcpy(h->E, E, sizeof(double) * h->esz, kind);
+  e = e ? e : cudaMemcpy(h->S, S, sizeof(double) * h->ssz, kind);
   e = e ? e : cudaMemset(h->status, 0, 8 * sizeof(int));
   if (e != cudaSuccess) {
     cudaFree(mem);
@@ -460,6 +629,7 @@ void hss_destroy(hss_t h) {
   cudaSetDevice(h->device);
   clear_trace(h);
   cudaFree(h->arena);
+  if (h->f32.arena) cudaFree(h->f32.arena);
   cudaSetDevice(cur);
   delete h;
 }
@@ -467,10 +637,26 @@ void hss_destroy(hss_t h) {
 int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
   if (!h) return HSS_ERR_INVALID_ARG;
   const int prec = opt ? opt->precision : HSS_FP64;
-  if (prec != HSS_FP64) return HSS_ERR_INVALID_ARG;   // mixed modes: not built yet
+  if (prec != HSS_FP64 && prec != HSS_MIXED_FP32) return HSS_ERR_INVALID_ARG;
+  if (opt && (opt->ir_max_it < 0 || !(opt->ir_tol >= 0.0))) return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
-  int rc = factorize_fp64(h, st);
+  if (prec != HSS_FP64 && !h->f32.arena) {
+    const size_t bytes = layout_f32(h, nullptr);
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return HSS_ERR_OOM;
+    }
+    h->f32.arena = mem;
+    h->f32.bytes = bytes;
+    layout_f32(h, static_cast<char*>(mem));
+  }
+  if (opt) {
+    h->ir_max_it = opt->ir_max_it;
+    h->ir_tol = opt->ir_tol;
+  }
+  int rc = factorize(h, prec, st);
   if (rc) return rc;
   h->precision = prec;
   h->factorized = 1;
@@ -483,13 +669,19 @@ int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, voi
   if (!h->factorized) return HSS_ERR_NOT_FACTORIZED;
   if (nrhs == 0) return HSS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->last_stream = st;
+  if (h->precision != HSS_FP64) return solve_ir(h, b, x, nrhs, ld, st);
   if (x != b) {
     cudaError_t e = cudaMemcpy2DAsync(x, sizeof(double) * ld, b, sizeof(double) * ld,
                                       sizeof(double) * h->n, nrhs, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return HSS_ERR_CUDA;
   }
-  h->last_stream = st;
-  return solve_fp64(h, x, nrhs, ld, st);
+  for (int j0 = 0; j0 < nrhs; j0 += kSolveCols) {
+    const int nc = std::min(kSolveCols, nrhs - j0);
+    int rc = solve_sweeps<double>(h, h->f64, x + (long long)j0 * ld, nc, ld, st);
+    if (rc) return rc;
+  }
+  return HSS_OK;
 }
 
 int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, void* stream) {
@@ -497,7 +689,7 @@ int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, vo
   if (nrhs == 0) return HSS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->last_stream = st;
-  return matvec_fp64(h, x, y, nrhs, ld, st);
+  return matvec_fp64(h, x, ld, y, ld, nrhs, st);
 }
 
 int hss_sync(hss_t h) {
@@ -548,7 +740,7 @@ int hss_trace(hss_t h, int32_t enable) {
 }
 
 int hss_trace_read(hss_t h, int32_t kind, double* ms, int64_t* launches, double* flops) {
-  if (!h || kind < 0 || kind >= HSS_K_COUNT) return HSS_ERR_INVALID_ARG;
+  if (!h || kind < 0 || kind >= 2 * HSS_K_COUNT) return HSS_ERR_INVALID_ARG;
   double tot = 0.0, fl = 0.0;
   long long cnt = 0;
   for (auto& r : h->trace) {
@@ -576,13 +768,13 @@ int hss_export(hss_t h, int32_t what, int32_t level, double* dst, size_t count) 
   if (!h || !dst || level < 0 || level > h->L) return HSS_ERR_INVALID_ARG;
   if (!h->factorized) return HSS_ERR_NOT_FACTORIZED;
   if (h->precision != HSS_FP64) return HSS_ERR_INVALID_ARG;
-  const Level& P = h->lv[level];
+  const LevelT<double>& P = h->f64.lv[level];
   const double* src = nullptr;
   size_t n = 0;
   const size_t r = h->rank;
   switch (what) {
     case 0: src = P.V; n = (size_t)P.n * P.b * r; break;
-    case 1: src = P.T; n = (size_t)P.n * r * r; break;
+    case 1: src = P.T_; n = (size_t)P.n * r * r; break;
     case 2: src = P.LB; n = (size_t)P.n * r * r; break;
     case 3: src = P.M; n = (size_t)P.n * P.b * P.b; break;
     case 4: src = P.B; n = (size_t)P.n * P.b * r; break;

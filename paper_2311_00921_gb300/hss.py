@@ -206,13 +206,16 @@ class HSS:
         _check(load().hss_trace(self._h, 1 if enable else 0), "hss_trace")
 
     def trace_read(self):
-        """{kernel: (ms, launches, algorithmic flops)} of the logged launches."""
+        """{"kernel.f64" / "kernel.f32": (ms, launches, algorithmic flops)} of the
+        logged launches (classes with no launch are left out)."""
         out = {}
-        for k, name in enumerate(self.KERNELS):
-            ms, n, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
-            _check(load().hss_trace_read(self._h, k, ctypes.byref(ms), ctypes.byref(n),
-                                         ctypes.byref(fl)), "hss_trace_read")
-            out[name] = (ms.value, n.value, fl.value)
+        for prec, off in (("f64", 0), ("f32", len(self.KERNELS))):
+            for k, name in enumerate(self.KERNELS):
+                ms, n, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+                _check(load().hss_trace_read(self._h, k + off, ctypes.byref(ms), ctypes.byref(n),
+                                             ctypes.byref(fl)), "hss_trace_read")
+                if n.value:
+                    out[f"{name}.{prec}"] = (ms.value, n.value, fl.value)
         return out
 
     def launch_count(self) -> int:

@@ -216,3 +216,57 @@ def test_full_size_sphere_yukawa_sampled():
     x_ref = O.solve(F, b)
     err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
     assert err.max() <= 1e-10, err.max()
+
+
+# ---------------------------------------------------------------- mixed precision + refinement
+@pytest.mark.parametrize("name,n,kw", [
+    ("cube_inv_4k", 4096, {}),
+    ("sphere_yukawa_256k", 8192, {}),
+    ("grid_exp_64k", 4096, {}),
+    ("sphere_yukawa_256k", 2048, {"leaf": 128, "rank": 48}),
+])
+def test_mixed_fp32_refinement(name, n, kw):
+    """FP32 factor as preconditioner, FP64 residual: reaches 1e-12 relative residual
+    per column and the FP64 oracle's solution within 1e-10."""
+    w = I.scaled(I.WORKLOADS[name], n, **kw)
+    h = I.build_hss(w)
+    dev = hss.HSS(h)
+    dev.factorize("fp32", ir_tol=1e-12, ir_max_it=30)
+    b = I.rhs(w.n, 5, w.seed + 3)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    info = dev.last_info()
+    assert info["code"] == 0 and info["ir_resid"] <= 1e-12 and info["ir_iters"] <= 10, info
+    res = b - O.matvec(h, x)
+    assert (np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)).max() <= 1e-12
+    F = O.factor(h)
+    x_ref = O.solve(F, b)
+    err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    assert err.max() <= 1e-10, err
+    # log det of the FP32 factor (root FP64): close to the FP64 value at FP32 accuracy
+    ld_ref = O.logdet(F)
+    assert abs(dev.logdet() - ld_ref) <= 1e-4 * abs(ld_ref)
+
+
+def test_mixed_fp32_in_place_and_many_columns():
+    h = I.random_hss(3, 64, 16, seed=12, orthonormal=False)
+    dev = hss.HSS(h)
+    dev.factorize("fp32")
+    F = O.factor(h)
+    b = I.rhs(h.n, 19, 4)        # two refinement passes of 16 + 3 columns
+    xb = hss.colmajor(b)
+    dev.solve(xb, xb)
+    x = xb.cpu().numpy()
+    x_ref = O.solve(F, b)
+    err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    assert err.max() <= 1e-10
+
+
+def test_mixed_refinement_reports_no_convergence():
+    h = I.random_hss(2, 32, 8, seed=3)
+    dev = hss.HSS(h)
+    dev.factorize("fp32", ir_tol=0.0, ir_max_it=2)   # tolerance 0 cannot be met
+    with pytest.raises(hss.HSSError) as ei:
+        dev.solve(hss.colmajor(np.ones(h.n)))
+    assert ei.value.code == -7
+    info = dev.last_info()
+    assert info["ir_iters"] == 2 and info["ir_resid"] < 1e-10
