@@ -195,6 +195,15 @@ size_t layout_f32(hss_s* h, char* base) {
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? HSS_OK : HSS_ERR_CUDA; }
 
+// a launcher's error: shared memory the device cannot give is a size problem,
+// anything else a CUDA failure
+#define HSS_TRY(call)                                                                  \
+  do {                                                                                 \
+    const cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess)                                                             \
+      return e_ == cudaErrorInvalidConfiguration ? HSS_ERR_INVALID_ARG : HSS_ERR_CUDA; \
+  } while (0)
+
 int check_launch() {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HSS_OK : HSS_ERR_CUDA;
@@ -284,7 +293,7 @@ int factor_levels(hss_s* h, Factor<T>& f, cudaStream_t st) {
     {
       Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, st,
                sizeof(T) == 4);
-      launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, st);
+      HSS_TRY(launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, st));
     }
     // (d, first half) merge: Ŝ = L_B(c2) S L_B(c1)ᵀ and Ŝᵀ into the parent's
     // off-diagonal blocks, parent basis blkdiag(L_B(c1), L_B(c2)) E_p
@@ -320,8 +329,8 @@ int factor_levels(hss_s* h, Factor<T>& f, cudaStream_t st) {
     // (c) partial Cholesky + (d, second half) Schur complements into the parent
     {
       Launch k(h, HSS_K_PCHOL, pchol_flops(b, c) * n, st, sizeof(T) == 4);
-      launch_pchol<T>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1), l, 0,
-                      h->status, n, st);
+      HSS_TRY(launch_pchol<T>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1), l, 0,
+                      h->status, n, st));
     }
     int rc = check_launch();
     if (rc) return rc;
@@ -367,8 +376,8 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
   const int b0 = 2 * r;
   {
     Launch k(h, HSS_K_PCHOL, pchol_flops(b0, b0), st);
-    launch_pchol<double>(root, b0, (long long)b0 * b0, b0, b0, nullptr, 0, 0, h->logdet_part, 0,
-                         0, h->status, 1, st);
+    HSS_TRY(launch_pchol<double>(root, b0, (long long)b0 * b0, b0, b0, nullptr, 0, 0, h->logdet_part, 0,
+                         0, h->status, 1, st));
   }
   {
     Launch k(h, HSS_K_OTHER, (double)((2LL << L) - 1), st);
@@ -389,8 +398,8 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     const int ldv = (l == L) ? ld : P.n * P.b;
     apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/true, st);
     Launch k(h, HSS_K_TRSV_FWD, trsv_flops(P.b, P.c, nc) * P.n, st, sizeof(T) == 4);
-    launch_trsv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                       Q.n * Q.b, r, P.n, st);
+    HSS_TRY(launch_trsv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                       Q.n * Q.b, r, P.n, st));
   }
   const int b0 = 2 * r;
   double* rootA;
@@ -406,11 +415,11 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
   }
   {
     Launch k(h, HSS_K_TRSV_FWD, trsv_flops(b0, b0, nc), st);
-    launch_trsv_fwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st);
+    HSS_TRY(launch_trsv_fwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st));
   }
   {
     Launch k(h, HSS_K_TRSV_BWD, trsv_flops(b0, b0, nc), st);
-    launch_trsv_bwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st);
+    HSS_TRY(launch_trsv_bwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st));
   }
   if (sizeof(T) != sizeof(double)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
@@ -423,8 +432,8 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     const int ldv = (l == L) ? ld : P.n * P.b;
     {
       Launch k(h, HSS_K_TRSV_BWD, trsv_flops(P.b, P.c, nc) * P.n, st, sizeof(T) == 4);
-      launch_trsv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                         Q.n * Q.b, r, P.n, st);
+      HSS_TRY(launch_trsv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                         Q.n * Q.b, r, P.n, st));
     }
     apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/false, st);
   }
@@ -767,22 +776,37 @@ int hss_launch_count(hss_t h, int64_t* out) {
 int hss_export(hss_t h, int32_t what, int32_t level, double* dst, size_t count) {
   if (!h || !dst || level < 0 || level > h->L) return HSS_ERR_INVALID_ARG;
   if (!h->factorized) return HSS_ERR_NOT_FACTORIZED;
-  if (h->precision != HSS_FP64) return HSS_ERR_INVALID_ARG;
-  const LevelT<double>& P = h->f64.lv[level];
-  const double* src = nullptr;
-  size_t n = 0;
+  const bool f32 = (h->precision != HSS_FP64);
   const size_t r = h->rank;
+  size_t n = 0;
+  const void* src = nullptr;
+  const int lb = (level == h->L) ? h->leaf : 2 * h->rank;
+  const size_t nodes = size_t(1) << level;
   switch (what) {
-    case 0: src = P.V; n = (size_t)P.n * P.b * r; break;
-    case 1: src = P.T_; n = (size_t)P.n * r * r; break;
-    case 2: src = P.LB; n = (size_t)P.n * r * r; break;
-    case 3: src = P.M; n = (size_t)P.n * P.b * P.b; break;
-    case 4: src = P.B; n = (size_t)P.n * P.b * r; break;
+    case 0: n = nodes * lb * r; break;
+    case 1: n = nodes * r * r; break;
+    case 2: n = nodes * r * r; break;
+    case 3: n = nodes * lb * lb; break;
+    case 4: n = nodes * lb * r; break;
     default: return HSS_ERR_INVALID_ARG;
+  }
+  if (f32) {
+    const LevelT<float>& P = h->f32.lv[level];
+    const float* ps[5] = {P.V, P.T_, P.LB, P.M, P.B};
+    src = ps[what];
+  } else {
+    const LevelT<double>& P = h->f64.lv[level];
+    const double* ps[5] = {P.V, P.T_, P.LB, P.M, P.B};
+    src = ps[what];
   }
   if (!src || n > count) return HSS_ERR_INVALID_ARG;
   if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return HSS_ERR_CUDA;
-  return cuda_err(cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (!f32) return cuda_err(cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost));
+  std::vector<float> tmp(n);
+  if (cudaMemcpy(tmp.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HSS_ERR_CUDA;
+  for (size_t i = 0; i < n; ++i) dst[i] = (double)tmp[i];
+  return HSS_OK;
 }
 
 }  // extern "C"

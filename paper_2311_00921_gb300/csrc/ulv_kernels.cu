@@ -19,6 +19,8 @@
 //  * logdet_reduce_kernel -- 2 Σ log diag over all nodes, fixed summation order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "ulv_kernels.cuh"
 
@@ -28,12 +30,93 @@ constexpr int NT = 256;
 constexpr int NB = 32;   // panel width of the blocked Cholesky / triangular solves
 
 // ------------------------------------------------------------------ QL
+// Sum over the 32 lanes of acc[k] lands in lane k (k < NV; NV = 16 or 32):
+// a transposing butterfly, NV - 1 (+ NV for NV = 16) shuffles instead of NV * 5.
+template <typename T, int NV>
+HSS_DEVINL T warp_transpose_reduce(T (&acc)[NV], int lane) {
+  if (NV == 16) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
+  }
+#pragma unroll
+  for (int s = NV / 2; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const T send = upper ? acc[i] : acc[i + s];
+      const T keep = upper ? acc[i + s] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return acc[0];
+}
+
+// reflector jj of the panel starting at column j0, row i (unit at j0 + jj, zero above)
 template <typename T>
+HSS_DEVINL T vpan(const T* P, int b, int j0, int jj, int i) {
+  const int d = j0 + jj;
+  return i > d ? P[i + jj * b] : (i == d ? T(1) : T(0));
+}
+
+// CTA-level product O(q, c) = Σ_{i >= i0} Pt(q, i) A(i, c) for q < NBP and the
+// ncols columns of A (column c at A + c * lda): the panel's reflectors (Pt,
+// transposed in shared memory with row pitch NBP + 1) against 64-row slabs of A
+// staged in shared memory.  Thread t owns reflector q = t % NBP and NBP / 8
+// consecutive columns of each 32-column chunk.  O(q, c) lands at Out[q * os1 + c * os2].
+template <typename T, int NBP>
+HSS_DEVINL void cta_vt_times(const T* Pt, const T* A, long long lda, int ncols, int i0, int b,
+                             T* As, T* Out, int os1, int os2) {
+  constexpr int CPT = NBP / 8;   // columns per thread per chunk
+  const int tid = threadIdx.x;
+  const int q = tid % NBP, cg = tid / NBP;
+  for (int c0 = 0; c0 < ncols; c0 += 32) {
+    T acc[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) acc[u] = T(0);
+    for (int s0 = i0; s0 < b; s0 += 64) {
+      for (int e = tid; e < 64 * 32; e += NT) {
+        const int ii = e % 64, cc = e / 64;
+        const int i = s0 + ii, c = c0 + cc;
+        As[ii * 33 + cc] = (i < b && c < ncols) ? A[i + (long long)c * lda] : T(0);
+      }
+      __syncthreads();
+      const int rows = min(64, b - s0);
+      for (int ii = 0; ii < rows; ++ii) {
+        const T v = Pt[q + (s0 + ii) * (NBP + 1)];
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) acc[u] = fma(v, As[ii * 33 + cg * CPT + u], acc[u]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + cg * CPT + u;
+      if (c < ncols) Out[q * os1 + c * os2] = acc[u];
+    }
+  }
+}
+
+// Blocked Householder QR of the reversed basis (= QL of the basis): panels of
+// NBP columns are factored in shared memory; the trailing columns get the
+// panel's block reflector, A -= Ṽ_p (T_pᵀ (Ṽ_pᵀ A)), as two CTA-level products;
+// the compact-WY T is assembled block by block,
+// T(0:j0, p) = -T(0:j0, 0:j0) (Ṽ_{0:j0}ᵀ Ṽ_p) T_p.
+template <typename T, int NBP>
 __global__ void __launch_bounds__(NT)
 ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                 long long sT, T* LB, long long sL, int b, int r) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Pt = reinterpret_cast<T*>(smem_raw);       // panel reflectors, transposed: (NBP+1) x b
+  T* P = Pt + (size_t)b * (NBP + 1);            // panel being factored, b x NBP (ld = b)
+  // after the panel factorization the P region holds the products' buffers
+  T* Ws = P;                                    // NBP x r : Ṽ_pᵀ A_trail, then T_pᵀ of it
+  T* Xs = Ws + (size_t)NBP * r;                 // r x NBP : Ṽ_{0:j0}ᵀ Ṽ_p
+  T* Ys = Xs + (size_t)r * NBP;                 // r x NBP
+  T* As = Ys + (size_t)r * NBP;                 // 64 x 33 staging slab
   __shared__ T red[32];
-  __shared__ T tau_s[512];
+  __shared__ T tau_s[256];
+  __shared__ T Tp[NBP][NBP + 1];
+  __shared__ T Gp[NBP][NBP + 1];
   __shared__ T beta_s;
   const long long node = blockIdx.x;
   const T* B = Bsrc + node * sB;
@@ -42,51 +125,159 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
   T* Ln = LB + node * sL;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
 
-  // reversed copy: W(i, j) = B(b-1-i, r-1-j)
   for (long long e = tid; e < (long long)b * r; e += NT) {
     const int i = (int)(e % b), j = (int)(e / b);
     W[i + (long long)j * b] = B[(b - 1 - i) + (long long)(r - 1 - j) * ldb_src];
   }
+  for (int e = tid; e < r * r; e += NT) Tn[e] = T(0);
   __syncthreads();
 
-  // unblocked Householder QR of W (b x r)
-  for (int j = 0; j < r; ++j) {
-    T* wj = W + (long long)j * b;
-    T s = T(0);
-    for (int i = j + 1 + tid; i < b; i += NT) s += wj[i] * wj[i];
-    const T sigma = block_sum(s, red);
-    const T alpha = wj[j];
-    T tau, beta, scale;
-    if (sigma == T(0)) {
-      tau = T(0);
-      beta = alpha;
-      scale = T(1);
-    } else {
-      const T nrm = sqrt(alpha * alpha + sigma);
-      beta = alpha >= T(0) ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      scale = T(1) / (alpha - beta);
+  for (int j0 = 0; j0 < r; j0 += NBP) {
+    const int nbw = min(NBP, r - j0);
+    for (int e = tid; e < (b - j0) * nbw; e += NT) {
+      const int i = j0 + e % (b - j0), jj = e / (b - j0);
+      P[i + jj * b] = W[i + (long long)(j0 + jj) * b];
     }
-    if (tid == 0) {
-      tau_s[j] = tau;
-      beta_s = beta;
-    }
-    for (int i = j + 1 + tid; i < b; i += NT) wj[i] *= scale;
     __syncthreads();
-    // apply H_j = I - tau v vᵀ (v_j = 1) to columns k > j, one warp per column
-    if (tau != T(0)) {
-      for (int k = j + 1 + wid; k < r; k += nw) {
-        T* wk = W + (long long)k * b;
-        T d = T(0);
-        for (int i = j + 1 + lane; i < b; i += 32) d += wj[i] * wk[i];
-        d = warp_sum(d) + wk[j];
-        const T f = tau * d;
-        for (int i = j + 1 + lane; i < b; i += 32) wk[i] -= f * wj[i];
-        if (lane == 0) wk[j] -= f;
+    // factor the panel in shared memory
+    for (int jj = 0; jj < nbw; ++jj) {
+      const int j = j0 + jj;
+      T* pj = P + jj * b;
+      T sq = T(0);
+      for (int i = j + 1 + tid; i < b; i += NT) sq += pj[i] * pj[i];
+      const T sigma = block_sum(sq, red);
+      const T alpha = pj[j];
+      T tau, beta, scale;
+      if (sigma == T(0)) {
+        tau = T(0);
+        beta = alpha;
+        scale = T(1);
+      } else {
+        const T nrm = sqrt(alpha * alpha + sigma);
+        beta = alpha >= T(0) ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scale = T(1) / (alpha - beta);
+      }
+      if (tid == 0) {
+        tau_s[j] = tau;
+        beta_s = beta;
+      }
+      for (int i = j + 1 + tid; i < b; i += NT) pj[i] *= scale;
+      __syncthreads();
+      if (tau != T(0)) {
+        for (int kk = jj + 1 + wid; kk < nbw; kk += nw) {
+          T* pk = P + kk * b;
+          T d = T(0);
+          for (int i = j + 1 + lane; i < b; i += 32) d += pj[i] * pk[i];
+          d = warp_sum(d) + pk[j];
+          const T f = tau * d;
+          for (int i = j + 1 + lane; i < b; i += 32) pk[i] -= f * pj[i];
+          if (lane == 0) pk[j] -= f;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) pj[j] = beta_s;   // R(j, j)
+      __syncthreads();
+    }
+    // write the panel back (R on and above the diagonal, reflectors below) and
+    // keep the reflectors, with their unit diagonal and zeros above, transposed
+    for (int e = tid; e < (b - j0) * nbw; e += NT) {
+      const int i = j0 + e % (b - j0), jj = e / (b - j0);
+      W[i + (long long)(j0 + jj) * b] = P[i + jj * b];
+    }
+    for (int e = tid; e < b * NBP; e += NT) {
+      const int i = e / NBP, q = e % NBP;
+      const int d = j0 + q;
+      T v = T(0);
+      if (q < nbw && i >= j0) v = i > d ? P[i + q * b] : (i == d ? T(1) : T(0));
+      Pt[q + i * (NBP + 1)] = v;
+    }
+    __syncthreads();
+    // panel Gram Gp(a, c) = v_aᵀ v_c (a < c) and panel T (forward dlarft)
+    for (int pr = wid; pr < nbw * nbw; pr += nw) {
+      const int a = pr % nbw, c = pr / nbw;
+      if (a >= c) continue;
+      T d = T(0);
+      for (int i = j0 + c + lane; i < b; i += 32)
+        d += Pt[a + i * (NBP + 1)] * Pt[c + i * (NBP + 1)];
+      d = warp_sum(d);
+      if (lane == 0) Gp[a][c] = d;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      for (int c = 0; c < nbw; ++c) {
+        T v = T(0);
+        if (lane < c) {
+          for (int m = lane; m < c; ++m) v += Tp[lane][m] * Gp[m][c];
+          v = -tau_s[j0 + c] * v;
+        }
+        __syncwarp();
+        if (lane < c) Tp[lane][c] = v;
+        if (lane == c) Tp[c][c] = tau_s[j0 + c];
+        if (lane > c && lane < NBP) Tp[lane][c] = T(0);
+        __syncwarp();
       }
     }
     __syncthreads();
-    if (tid == 0) wj[j] = beta_s;   // R(j, j)
+    // T(0:j0, panel) = -T(0:j0, 0:j0) (Ṽ_{0:j0}ᵀ Ṽ_p) T_p ; T(panel, panel) = T_p
+    if (j0 > 0) {
+      // Xs(a, q) = v_aᵀ v_q over rows >= j0 (where v_a, a < j0, is below its diagonal)
+      cta_vt_times<T, NBP>(Pt, W, b, j0, j0, b, As, Xs, 1, NBP);
+    }
+    __syncthreads();
+    if (j0 > 0) {
+      for (int e = tid; e < j0 * nbw; e += NT) {   // Y = T(0:j0, 0:j0) X
+        const int a = e % j0, q = e / j0;
+        T v = T(0);
+        for (int m = a; m < j0; ++m) v += Tn[a + (long long)m * r] * Xs[q + m * NBP];
+        Ys[a + q * r] = v;
+      }
+      __syncthreads();
+      for (int e = tid; e < j0 * nbw; e += NT) {   // T(0:j0, panel) = -Y T_p
+        const int a = e % j0, q = e / j0;
+        T v = T(0);
+        for (int m = 0; m <= q; ++m) v += Ys[a + m * r] * Tp[m][q];
+        Tn[a + (long long)(j0 + q) * r] = -v;
+      }
+    }
+    for (int e = tid; e < nbw * nbw; e += NT) {
+      const int a = e % nbw, q = e / nbw;
+      Tn[(j0 + a) + (long long)(j0 + q) * r] = Tp[a][q];
+    }
+    // trailing columns k >= j0 + nbw: A_k -= Ṽ_p T_pᵀ (Ṽ_pᵀ A_k)
+    const int k0 = j0 + nbw, nk = r - k0;
+    if (nk > 0) {
+      cta_vt_times<T, NBP>(Pt, W + (long long)k0 * b, b, nk, j0, b, As, Ws, 1, NBP);
+      __syncthreads();
+      // Ys(:, k) = T_pᵀ Ws(:, k)
+      for (int e = tid; e < nk * NBP; e += NT) {
+        const int c = e % NBP, k = e / NBP;
+        T v = T(0);
+        for (int a = 0; a <= c; ++a) v += Tp[a][c] * Ws[a + k * NBP];
+        Ys[c + k * NBP] = v;
+      }
+      __syncthreads();
+      // A(i, k) -= Σ_q v_q(i) Ys(q, k): thread owns a row and 8 columns per pass
+      const int rows = b - j0;
+      for (int c0 = 0; c0 < nk; c0 += 8 * (NT / 64)) {
+        const int cb = c0 + (tid / 64) * 8;
+        for (int ii = tid % 64; ii < rows; ii += 64) {
+          const int i = j0 + ii;
+          T acc[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] = T(0);
+#pragma unroll 4
+          for (int q = 0; q < NBP; ++q) {
+            const T v = Pt[q + i * (NBP + 1)];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = fma(v, Ys[q + (cb + u) * NBP], acc[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (cb + u < nk) W[i + (long long)(k0 + cb + u) * b] -= acc[u];
+        }
+      }
+    }
     __syncthreads();
   }
 
@@ -104,38 +295,6 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
     if (i <= j) W[i + (long long)j * b] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
-  // Gram G = Ṽᵀ Ṽ, upper part stored transposed in the strict lower triangle of T
-  for (int e = wid; e < r * r; e += nw) {
-    const int i = e % r, j = e / r;
-    if (i >= j) continue;   // need G(i, j) for i < j
-    const T* vi = W + (long long)i * b;
-    const T* vj = W + (long long)j * b;
-    T d = T(0);
-    for (int t = j + lane; t < b; t += 32) d += vi[t] * vj[t];   // vj is zero above row j
-    d = warp_sum(d);
-    if (lane == 0) Tn[j + (long long)i * r] = d;   // G(i,j) at T(j,i)
-  }
-  __syncthreads();
-  // forward columnwise T (dlarft): T(j,j) = tau_j, T(0:j, j) = -tau_j T(0:j,0:j) G(0:j, j)
-  for (int j = 0; j < r; ++j) {
-    const T tj = tau_s[j];
-    T val = T(0);
-    const int i = tid;
-    if (i < j) {
-      T acc = T(0);
-      for (int m = i; m < j; ++m) acc += Tn[i + (long long)m * r] * Tn[j + (long long)m * r];
-      val = -tj * acc;
-    }
-    __syncthreads();
-    if (tid < j) Tn[tid + (long long)j * r] = val;   // r <= NT is checked by the host
-    if (tid == 0) Tn[j + (long long)j * r] = tj;
-    __syncthreads();
-  }
-  // zero the strict lower triangle (the Gram scratch)
-  for (int e = tid; e < r * r; e += NT) {
-    const int i = e % r, j = e / r;
-    if (i > j) Tn[i + (long long)j * r] = T(0);
-  }
   // back to natural row order: V = F_b Ṽ
   for (long long e = tid; e < (long long)(b / 2) * r; e += NT) {
     const int i = (int)(e % (b / 2)), j = (int)(e / (b / 2));
@@ -201,13 +360,24 @@ pchol_kernel(T* Mb, int ldm, long long sM, int b, int c, T* PA, int ldpa, long l
     }
     __syncthreads();
     if (fail) return;
-    // panel TRSM: rows kb..n1-1 : x L_diagᵀ = m
+    // panel TRSM: rows kb..n1-1 solve x L_diagᵀ = m, right-looking on a row held
+    // in registers (critical path kb steps, independent updates within a step)
     for (int i = kb + tid; i < n1; i += NT) {
-      for (int jj = 0; jj < kb; ++jj) {
-        T x = P[i + jj * b];
-        for (int t = 0; t < jj; ++t) x -= P[i + t * b] * P[jj + t * b];
-        P[i + jj * b] = x / P[jj + jj * b];
+      T x[NB];
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj) x[jj] = jj < kb ? P[i + jj * b] : T(0);
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj) {
+        if (jj < kb) {
+          x[jj] = x[jj] / P[jj + jj * b];
+#pragma unroll
+          for (int t = jj + 1; t < NB; ++t)
+            if (t < kb) x[t] = fma(-x[jj], P[t + jj * b], x[t]);
+        }
       }
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj)
+        if (jj < kb) P[i + jj * b] = x[jj];
     }
     __syncthreads();
     // write the panel back (lower part of the diagonal block and everything below)
@@ -368,13 +538,25 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int k0 = bi * NB;
     const int kb = min(NB, c - k0);
-    // z_t -= sum_{i >= k0+kb} L(i, t) x_i  for t in the block
-    for (int e = tid; e < kb * nrhs; e += NT) {
-      const int t = e % kb, j = e / kb;
+    // z_t -= sum_{i >= k0+kb} L(i, t) x_i for t in the block: one warp per t,
+    // lanes over i, every right-hand side at once, then warp reductions
+    for (int t = wid; t < kb; t += nw) {
       const T* lcol = M + (long long)(k0 + t) * ldm;
-      T acc = T(0);
-      for (int i = k0 + kb; i < b; ++i) acc = fma(lcol[i], y[i + j * b], acc);
-      y[(k0 + t) + j * b] -= acc;
+      T acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = T(0);
+      for (int i = k0 + kb + lane; i < b; i += 32) {
+        const T l = lcol[i];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j < nrhs) acc[j] = fma(l, y[i + j * b], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j >= nrhs) break;
+        const T sum = warp_sum(acc[j]);
+        if (lane == 0) y[(k0 + t) + j * b] -= sum;
+      }
     }
     __syncthreads();
     // diagonal block, transposed back substitution
@@ -417,54 +599,74 @@ __global__ void logdet_reduce_kernel(const double* part, int n, double* out) {
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+// opt a kernel into `bytes` of dynamic shared memory (plus its static part);
+// false if the device cannot give that much
+// (the 48 KB default holds static + dynamic shared memory together)
+template <typename K>
+bool smem_opt_in(K kernel, size_t bytes) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+  if (bytes + fa.sharedSizeBytes <= 48 * 1024) return true;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (bytes + fa.sharedSizeBytes > (size_t)optin) return false;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return true;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+         cudaSuccess;
+}
+
 template <typename T>
-void launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
-                     long long sT, T* LB, long long sL, int b, int r, int nodes, cudaStream_t st) {
-  ql_basis_kernel<T><<<nodes, NT, 0, st>>>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r);
+size_t ql_smem(int b, int r) {
+  constexpr int NBP = sizeof(T) == 8 ? 16 : 32;
+  const size_t region = std::max<size_t>((size_t)b * NBP, (size_t)3 * NBP * r + 64 * 33);
+  return ((size_t)b * (NBP + 1) + region) * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
+                            long long sT, T* LB, long long sL, int b, int r, int nodes,
+                            cudaStream_t st) {
+  // panel width: 16 columns in FP64, 32 in FP32 (the panel lives in shared memory)
+  constexpr int NBP = sizeof(T) == 8 ? 16 : 32;
+  const size_t sm = ql_smem<T>(b, r);
+  if (!smem_opt_in(ql_basis_kernel<T, NBP>, sm)) return cudaErrorInvalidConfiguration;
+  ql_basis_kernel<T, NBP><<<nodes, NT, sm, st>>>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r);
+  return cudaGetLastError();
 }
 
 template <typename T>
 size_t pchol_smem(int b) { return (size_t)b * NB * sizeof(T); }
 
 template <typename T>
-void launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int ldpa, long long sPA,
-                  double* logdet_part, int level, int node0, int* status, int nodes,
-                  cudaStream_t st) {
+cudaError_t launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int ldpa, long long sPA,
+                         double* logdet_part, int level, int node0, int* status, int nodes,
+                         cudaStream_t st) {
   const size_t sm = pchol_smem<T>(b);
-  static bool attr_set = false;   // per template instance
-  if (!attr_set) {
-    cudaFuncSetAttribute(pchol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  if (!smem_opt_in(pchol_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
   pchol_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, PA, ldpa, sPA, logdet_part, level,
                                          node0, status);
+  return cudaGetLastError();
 }
 
 template <typename T>
-void launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
-                     int nrhs, T* Par, int ldpar, long long sPar, int nodes, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(trsv_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr_set = true;
-  }
+cudaError_t launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
+                            long long sX, int nrhs, T* Par, int ldpar, long long sPar, int nodes,
+                            cudaStream_t st) {
   const size_t sm = (size_t)b * nrhs * sizeof(T);
+  if (!smem_opt_in(trsv_fwd_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
   trsv_fwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar);
+  return cudaGetLastError();
 }
 
 template <typename T>
-void launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
-                     int nrhs, const T* Par, int ldpar, long long sPar, int nodes,
-                     cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(trsv_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr_set = true;
-  }
+cudaError_t launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
+                            long long sX, int nrhs, const T* Par, int ldpar, long long sPar,
+                            int nodes, cudaStream_t st) {
   const size_t sm = (size_t)b * nrhs * sizeof(T);
+  if (!smem_opt_in(trsv_bwd_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
   trsv_bwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar);
+  return cudaGetLastError();
 }
 
 void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t st) {
@@ -472,13 +674,14 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
 }
 
 #define INST(T)                                                                                  \
-  template void launch_ql_basis<T>(const T*, int, long long, T*, long long, T*, long long, T*,    \
-                                   long long, int, int, int, cudaStream_t);                       \
-  template void launch_pchol<T>(T*, int, long long, int, int, T*, int, long long, double*, int,   \
-                                int, int*, int, cudaStream_t);                                    \
-  template void launch_trsv_fwd<T>(const T*, int, long long, int, int, T*, int, long long, int,   \
-                                   T*, int, long long, int, cudaStream_t);                        \
-  template void launch_trsv_bwd<T>(const T*, int, long long, int, int, T*, int, long long, int,   \
-                                   const T*, int, long long, int, cudaStream_t);
+  template cudaError_t launch_ql_basis<T>(const T*, int, long long, T*, long long, T*, long long,  \
+                                          T*, long long, int, int, int, cudaStream_t);            \
+  template cudaError_t launch_pchol<T>(T*, int, long long, int, int, T*, int, long long, double*, \
+                                       int, int, int*, int, cudaStream_t);                        \
+  template cudaError_t launch_trsv_fwd<T>(const T*, int, long long, int, int, T*, int, long long, \
+                                          int, T*, int, long long, int, cudaStream_t);            \
+  template cudaError_t launch_trsv_bwd<T>(const T*, int, long long, int, int, T*, int, long long, \
+                                          int, const T*, int, long long, int, cudaStream_t);      \
+  template size_t ql_smem<T>(int, int);
 INST(double)
 INST(float)

@@ -3,24 +3,28 @@
 #include <cuda_runtime.h>
 
 template <typename T>
-void launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
+cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                      long long sT, T* LB, long long sL, int b, int r, int nodes, cudaStream_t st);
 
 template <typename T>
 size_t pchol_smem(int b);
 
 template <typename T>
-void launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int ldpa, long long sPA,
+cudaError_t launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int ldpa, long long sPA,
                   double* logdet_part, int level, int node0, int* status, int nodes,
                   cudaStream_t st);
 
 template <typename T>
-void launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
+cudaError_t launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
                      int nrhs, T* Par, int ldpar, long long sPar, int nodes, cudaStream_t st);
 
 template <typename T>
-void launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
+cudaError_t launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx, long long sX,
                      int nrhs, const T* Par, int ldpar, long long sPar, int nodes,
                      cudaStream_t st);
 
 void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t st);
+
+// dynamic shared memory of the basis-completion kernel for a b x r basis
+template <typename T>
+size_t ql_smem(int b, int r);

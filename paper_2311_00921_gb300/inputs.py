@@ -447,3 +447,35 @@ def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
     """N(0,1) right-hand sides, column-major n x nrhs as a Fortran-ordered array."""
     rng = np.random.default_rng(seed)
     return np.asfortranarray(rng.standard_normal((n, nrhs)))
+
+
+def cached_build(w: Workload, cache_dir: Optional[str], **kw) -> HSSMatrix:
+    """build_hss(w), memoised in ``cache_dir`` (an .npz per workload and seed)
+    so that repeated runs on one machine skip the generation."""
+    if not cache_dir:
+        return build_hss(w, **kw)
+    import os
+    os.makedirs(cache_dir, exist_ok=True)
+    key = f"{w.name}_n{w.n}_l{w.leaf}_r{w.rank}_s{w.seed}_{kw.get('mode', 'spd')}.npz"
+    path = os.path.join(cache_dir, key.replace("@", "_"))
+    L = w.levels
+    if os.path.exists(path):
+        z = np.load(path)
+        D = list(z["D"])
+        U = list(z["U"])
+        E = {l: list(z[f"E{l}"]) for l in range(1, L)}
+        S = {l: list(z[f"S{l}"]) for l in range(1, L + 1)}
+        ranks = {l: z[f"R{l}"] for l in range(1, L + 1)}
+        return HSSMatrix(levels=L, sizes=z["sizes"], ranks=ranks, D=D, U=U, E=E, S=S,
+                         perm=z["perm"], points=z["points"], workload=w)
+    h = build_hss(w, **kw)
+    if h.uniform:
+        arrs = {"D": np.stack(h.D), "U": np.stack(h.U), "sizes": h.sizes, "perm": h.perm,
+                "points": h.points}
+        arrs.update({f"E{l}": np.stack(h.E[l]) for l in range(1, L)})
+        arrs.update({f"S{l}": np.stack(h.S[l]) for l in range(1, L + 1)})
+        arrs.update({f"R{l}": h.ranks[l] for l in range(1, L + 1)})
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, **arrs)
+        os.replace(tmp, path)
+    return h

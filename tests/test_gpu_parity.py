@@ -270,3 +270,26 @@ def test_mixed_refinement_reports_no_convergence():
     assert ei.value.code == -7
     info = dev.last_info()
     assert info["ir_iters"] == 2 and info["ir_resid"] < 1e-10
+
+
+@pytest.mark.parametrize("levels,leaf,rank", [(3, 100, 13), (2, 256, 32), (3, 128, 48)])
+def test_per_step_fp32_factor(levels, leaf, rank):
+    """The FP32 factor against the oracle run in float32 (LAPACK sgeqrf / spotrf
+    order of operations differs, so the bound is a few hundred FP32 ulps of the
+    block's scale)."""
+    h = I.random_hss(levels, leaf, rank, seed=levels * 7 + rank, orthonormal=False)
+    dev = hss.HSS(h)
+    dev.factorize("fp32")
+    F = O.factor(h, dtype=np.float32)
+    for l in range(levels, 0, -1):
+        V, T, LB, M = (dev.export(k, l) for k in ("V", "T", "LB", "M"))
+        for i in range(2 ** l):
+            b, r = V.shape[1], V.shape[2]
+            c = b - r
+            check_close(q_from_vt(V[i], T[i]), F.Q[l][i].astype(np.float64), 2e-4, f"Q32 l={l} i={i}")
+            check_close(LB[i], F.LB[l][i].astype(np.float64), 2e-4, f"L_B32 l={l} i={i}")
+            if c:
+                check_close(np.tril(M[i][:c, :c]), F.LRR[l][i].astype(np.float64), 1e-3,
+                            f"L^RR32 l={l} i={i}")
+            check_close(np.tril(M[i][c:, c:]), np.tril(F.SS[l][i]).astype(np.float64), 1e-3,
+                        f"SS32 l={l} i={i}")
