@@ -60,9 +60,12 @@ typedef struct hss_s* hss_t;
  * precision and use the factor as the preconditioner of FP64 iterative
  * refinement in hss_solve; the root Cholesky, residual and update are FP64.
  * HSS_MIXED_FP32: every per-level step in FP32 (FP32 accumulation).
- * HSS_MIXED_TF32 / HSS_MIXED_BF16: the dense contractions of the diagonal
- * product on tensor cores; hss_factorize returns HSS_ERR_INVALID_ARG for a
- * mode this build does not provide. */
+ * HSS_MIXED_TF32 / HSS_MIXED_BF16: as FP32, but the two dense contractions of
+ * the diagonal product (W = A V and A - Y'Vᵀ - V Y'ᵀ) run on the tensor cores
+ * (tcgen05) with TF32 / BF16 inputs and FP32 accumulation in tensor memory;
+ * every operand is split into hi + lo input-type parts and hi·hi + hi·lo + lo·hi
+ * is accumulated, so the contraction keeps most of the FP32 accuracy that the
+ * refinement needs. */
 typedef enum {
   HSS_FP64 = 0,
   HSS_MIXED_TF32 = 1,
@@ -186,8 +189,10 @@ typedef enum {
   HSS_K_TRSV_FWD = 5,  /* forward triangular sweep of the solve */
   HSS_K_TRSV_BWD = 6,  /* backward triangular sweep of the solve */
   HSS_K_OTHER = 7,     /* log-det reduction, precision conversion, refinement helpers */
-  HSS_K_COUNT = 8,
-  HSS_K_FP32 = 8       /* added to a class: the same kernel run in FP32 (mixed modes) */
+  HSS_K_TC_GEMM = 8,   /* tensor-core (tcgen05) W = A V of the mixed diagonal product */
+  HSS_K_TC_SYR2K = 9,  /* tensor-core (tcgen05) rank-2r update of the mixed diagonal product */
+  HSS_K_COUNT = 10,
+  HSS_K_FP32 = 10      /* added to a class: the same kernel run in FP32 (mixed modes) */
 } hss_kernel_kind;
 
 /* Per-kernel timing: with enable = 1 every later launch of the object is

@@ -17,7 +17,10 @@
 #include "../../include/hss.h"
 #include "common.cuh"
 #include "ir_kernels.cuh"
+#include "tc_gemm.cuh"
 #include "ulv_kernels.cuh"
+
+#include <type_traits>
 
 namespace {
 
@@ -70,6 +73,8 @@ struct hss_s {
   size_t arena_bytes = 0;
   int factorized = 0;
   int precision = HSS_FP64;
+  int use_tc = 0;                      // tensor-core contractions in the FP32 factor
+  TcMode tc_mode = TcMode::TF32x3;
   int ir_max_it = 30;
   double ir_tol = 1e-12;
   cudaStream_t last_stream = nullptr;
@@ -317,12 +322,30 @@ int factor_levels(hss_s* h, Factor<T>& f, cudaStream_t st) {
     // (b) diagonal product Â = Qᵀ A Q with Q = I - V T Vᵀ, in the symmetric
     // compact-WY form Â = A - Y'Vᵀ - V Y'ᵀ, Y' = A V T - ½ V Tᵀ Vᵀ A V T
     const T* Ain = (l == L) ? f.D : P.A;
-    gemm<T>(h, false, false, b, r, b, T(1), Ain, b, bb, P.V, b, br, T(0), f.W, b, br, n, st);
+    bool tc = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (h->use_tc) {
+        tc = true;
+        Launch k(h, HSS_K_TC_GEMM, 2.0 * b * r * (double)b * n, st);
+        if (tc_gemm(h->tc_mode, b, r, b, Ain, b, bb, P.V, b, br, /*b_ncontig=*/false, f.W, b, br,
+                    n, h->status, st) != cudaSuccess)
+          return HSS_ERR_CUDA;
+      }
+    }
+    if (!tc)
+      gemm<T>(h, false, false, b, r, b, T(1), Ain, b, bb, P.V, b, br, T(0), f.W, b, br, n, st);
     gemm<T>(h, false, false, b, r, r, T(1), f.W, b, br, P.T_, r, rr, T(0), f.Y, b, br, n, st);
     gemm<T>(h, true, false, r, r, b, T(1), P.V, b, br, f.Y, b, br, T(0), f.X, r, rr, n, st);
     gemm<T>(h, true, false, r, r, r, T(1), P.T_, r, rr, f.X, r, rr, T(0), f.Z, r, rr, n, st);
     gemm<T>(h, false, false, b, r, r, T(-0.5), P.V, b, br, f.Z, r, rr, T(1), f.Y, b, br, n, st);
-    {
+    if (tc) {
+      if constexpr (std::is_same<T, float>::value) {
+        Launch k(h, HSS_K_TC_SYR2K, 2.0 * r * b * (b + 1.0) * n, st);
+        if (tc_syr2k_lower(h->tc_mode, b, r, Ain, b, bb, f.Y, b, br, P.V, b, br, P.M, b, bb, n,
+                           h->status, st) != cudaSuccess)
+          return HSS_ERR_CUDA;
+      }
+    } else {
       Launch k(h, HSS_K_SYR2K, 2.0 * r * b * (b + 1.0) * n, st, sizeof(T) == 4);
       syr2k_lower_batched<T>(b, r, Ain, b, bb, f.Y, b, br, P.V, b, br, P.M, b, bb, n, st);
     }
@@ -646,7 +669,9 @@ void hss_destroy(hss_t h) {
 int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
   if (!h) return HSS_ERR_INVALID_ARG;
   const int prec = opt ? opt->precision : HSS_FP64;
-  if (prec != HSS_FP64 && prec != HSS_MIXED_FP32) return HSS_ERR_INVALID_ARG;
+  if (prec != HSS_FP64 && prec != HSS_MIXED_FP32 && prec != HSS_MIXED_TF32 &&
+      prec != HSS_MIXED_BF16)
+    return HSS_ERR_INVALID_ARG;
   if (opt && (opt->ir_max_it < 0 || !(opt->ir_tol >= 0.0))) return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
@@ -665,6 +690,8 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     h->ir_max_it = opt->ir_max_it;
     h->ir_tol = opt->ir_tol;
   }
+  h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
+  h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;
   int rc = factorize(h, prec, st);
   if (rc) return rc;
   h->precision = prec;

@@ -200,7 +200,8 @@ class HSS:
         return {"code": code, "level": lvl.value, "node": node.value, "col": col.value,
                 "ir_iters": it.value, "ir_resid": res.value}
 
-    KERNELS = ("ql", "gemm", "gemm_skinny", "syr2k", "pchol", "trsv_fwd", "trsv_bwd", "other")
+    KERNELS = ("ql", "gemm", "gemm_skinny", "syr2k", "pchol", "trsv_fwd", "trsv_bwd", "other",
+               "tc_gemm", "tc_syr2k")
 
     def trace(self, enable: bool):
         _check(load().hss_trace(self._h, 1 if enable else 0), "hss_trace")
