@@ -170,7 +170,8 @@ def traffic_record(kernel):
     return None
 
 
-KERNEL_SOURCES = {"gemm": "gemm_tile_kernel", "syr2k": "syr2k_lower_kernel",
+KERNEL_SOURCES = {"tc_gemm": "tc_gemm_kernel", "tc_syr2k": "tc_gemm_kernel",
+                  "gemm": "gemm_tile_kernel", "syr2k": "syr2k_lower_kernel",
                   "pchol": "pchol_kernel", "ql": "ql_basis_kernel",
                   "gemm_skinny": "gemm_n16_kernel", "trsv_fwd": "trsv_fwd_kernel",
                   "trsv_bwd": "trsv_bwd_kernel", "other": "logdet_reduce_kernel"}
@@ -251,11 +252,32 @@ def measured_peaks(torch):
         best = min(best, e0.elapsed_time(e1) / 1e3)
     del a, b
     peaks["f32"] = 2 * 8192 ** 3 / best / 1e12
+    for name, dt, tf32 in (("tf32", torch.float32, True), ("bf16", torch.bfloat16, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(8192, 8192, dtype=dt, device="cuda")
+        b = torch.randn(8192, 8192, dtype=dt, device="cuda")
+        a @ b
+        torch.cuda.synchronize()
+        best = 1e9
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        peaks[name] = 2 * 8192 ** 3 / best / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
     return peaks
 
 
 PEAK_SOURCE = {"f64": "cuBLAS DGEMM 8192^3 (FP64 pipe) measured in this run",
-               "f32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured in this run"}
+               "f32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured in this run",
+               "tf32": "cuBLAS TF32 GEMM 8192^3 measured in this run (x3 split: 3 MMAs per "
+                       "algorithmic product, so frac <= 1/3)",
+               "bf16": "cuBLAS BF16 GEMM 8192^3 measured in this run (x3 split: 3 MMAs per "
+                       "algorithmic product, so frac <= 1/3)"}
 
 
 def timed_steps(torch, dev, b, x, prec, steps, clocks=None):
@@ -291,10 +313,12 @@ def timed_steps(torch, dev, b, x, prec, steps, clocks=None):
     return out
 
 
-def roofline_of(tr, peaks, steps):
+def roofline_of(tr, peaks, steps, prec_mode="fp64"):
     dom = max(tr, key=lambda k: tr[k][0])
     dms, dn, dfl = tr[dom]
     kind, prec = dom.split(".")
+    if kind.startswith("tc_"):
+        prec = prec_mode   # tensor-core kernels: the MMA input type's peak
     achieved = dfl / (dms / 1e3) / 1e12 if dms > 0 else 0.0
     kname = KERNEL_SOURCES[kind]
     peak = peaks.get(prec) if peaks else None
@@ -302,7 +326,7 @@ def roofline_of(tr, peaks, steps):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if peak else None,
             "traffic": traffic_record(kname) if prec == "f64" else None,
-            "kernel": f"{kname} ({'FP64' if prec == 'f64' else 'FP32'})",
+            "kernel": f"{kname} ({ {'f64': 'FP64', 'f32': 'FP32', 'tf32': 'TF32 x3', 'bf16': 'BF16 x3'}.get(prec, prec)})",
             "peak_source": PEAK_SOURCE.get(prec),
             "kernel_ms_per_launch": dms / max(1, dn), "kernel_share": dms / total,
             "per_kernel_ms_per_step": {k: v[0] / steps for k, v in sorted(tr.items())},
@@ -407,7 +431,7 @@ def run_ours(args):
                "check": {"max_rel_residual": rel, "logdet": logdet,
                          "ir_iterations": info["ir_iters"], "ir_resid": info["ir_resid"]},
                "fp64": fp64,
-               "roofline": roofline_of(head["trace"], peaks, args.steps),
+               "roofline": roofline_of(head["trace"], peaks, args.steps, prec),
                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
                "gpu_launches": head["launches"]}
         print(json.dumps(out), flush=True)

@@ -78,6 +78,12 @@ struct hss_s {
   int ir_max_it = 30;
   double ir_tol = 1e-12;
   cudaStream_t last_stream = nullptr;
+  // basis-completion chain runs ahead on its own stream; one event per level
+  cudaStream_t qstream = nullptr;
+  std::vector<cudaEvent_t> ev_level;
+  cudaEvent_t ev_start = nullptr;
+  double* zq64 = nullptr;              // merge scratch of the basis chain (n_L/2 x r x r)
+  float* zq32 = nullptr;
   int ir_iters = 0;
   double ir_resid = 0.0;
   // launch accounting and the optional per-launch event log
@@ -168,6 +174,7 @@ size_t layout_main(hss_s* h, char* base) {
     h->xh[l] = bp.take<double>((size_t(1) << l) * r * kMaxCols);
     h->yh[l] = bp.take<double>((size_t(1) << l) * r * kMaxCols);
   }
+  h->zq64 = bp.take<double>((size_t)nL * r * r);
   h->R0 = bp.take<double>((size_t)4 * r * r);
   h->root_vec = bp.take<double>((size_t)2 * r * kSolveCols);
   h->rbuf = bp.take<double>((size_t)h->n * kSolveCols);
@@ -191,6 +198,7 @@ size_t layout_f32(hss_s* h, char* base) {
   f.Sc = bp.take<float>(h->ssz);
   layout_factor<float>(bp, f, L, leaf, r);
   f.d = bp.take<float>((size_t)h->n * kSolveCols);
+  h->zq32 = bp.take<float>((size_t)nL * r * r);
   f.D = f.Dc;
   f.U = f.Uc;
   f.E = f.Ec;
@@ -283,22 +291,31 @@ void apply_q(hss_s* h, Factor<T>& f, const LevelT<T>& P, T* vec, int ldv, int nc
           b, n, st);
 }
 
-// levels L .. 1 of Alg. 2; leaves the merged root block in f.lv[0].A
+// levels L .. 1 of Alg. 2; leaves the merged root block in f.lv[0].A.
+// Two chains: the basis chain (basis completion of level l, then the merge's
+// rescaled coupling Ŝ and the parent basis, which need only L_B of level l) runs
+// ahead on h->qstream; the main chain (diagonal product and partial Cholesky of
+// level l) waits for level l's basis event.  The levels' basis completions,
+// latency-bound at the top of the tree, thus overlap the main chain.
 template <typename T>
-int factor_levels(hss_s* h, Factor<T>& f, cudaStream_t st) {
+int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st) {
   const int L = h->L, r = h->rank;
   const long long rr = (long long)r * r;
+  cudaStream_t qs = h->qstream;
+  if (cudaEventRecord(h->ev_start, st) != cudaSuccess) return HSS_ERR_CUDA;
+  if (cudaStreamWaitEvent(qs, h->ev_start, 0) != cudaSuccess) return HSS_ERR_CUDA;
+  // basis chain
   for (int l = L; l >= 1; --l) {
     LevelT<T>& P = f.lv[l];
     LevelT<T>& Q = f.lv[l - 1];
-    const int b = P.b, n = P.n, c = P.c;
-    const long long br = (long long)b * r, bb = (long long)b * b;
+    const int b = P.b, n = P.n;
+    const long long br = (long long)b * r;
     // (a) basis completion (Eq. 2-3)
     const T* Bsrc = (l == L) ? f.U : P.B;
     {
-      Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, st,
+      Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, qs,
                sizeof(T) == 4);
-      HSS_TRY(launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, st));
+      HSS_TRY(launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, qs));
     }
     // (d, first half) merge: Ŝ = L_B(c2) S L_B(c1)ᵀ and Ŝᵀ into the parent's
     // off-diagonal blocks, parent basis blkdiag(L_B(c1), L_B(c2)) E_p
@@ -306,19 +323,32 @@ int factor_levels(hss_s* h, Factor<T>& f, cudaStream_t st) {
     const T* Sl = f.S + h->Soff[l];
     const int ldq = 2 * r;
     const long long sq = 4 * rr;
-    gemm<T>(h, false, false, r, r, r, T(1), P.LB + rr, r, 2 * rr, Sl, r, rr, T(0), f.Z, r, rr, np,
-            st);
-    gemm<T>(h, false, true, r, r, r, T(1), f.Z, r, rr, P.LB, r, 2 * rr, T(0), Q.A + r, ldq, sq, np,
-            st);
-    gemm<T>(h, false, true, r, r, r, T(1), P.LB, r, 2 * rr, f.Z, r, rr, T(0),
-            Q.A + (long long)r * ldq, ldq, sq, np, st);
+    gemm<T>(h, false, false, r, r, r, T(1), P.LB + rr, r, 2 * rr, Sl, r, rr, T(0), zq, r, rr, np,
+            qs);
+    gemm<T>(h, false, true, r, r, r, T(1), zq, r, rr, P.LB, r, 2 * rr, T(0), Q.A + r, ldq, sq, np,
+            qs);
+    gemm<T>(h, false, true, r, r, r, T(1), P.LB, r, 2 * rr, zq, r, rr, T(0),
+            Q.A + (long long)r * ldq, ldq, sq, np, qs);
     if (l - 1 >= 1) {
       const T* Ep = f.E + h->Eoff[l - 1];
       gemm<T>(h, false, false, r, r, r, T(1), P.LB, r, 2 * rr, Ep, 2 * r, 2 * rr, T(0), Q.B, 2 * r,
-              2 * rr, np, st);
+              2 * rr, np, qs);
       gemm<T>(h, false, false, r, r, r, T(1), P.LB + rr, r, 2 * rr, Ep + r, 2 * r, 2 * rr, T(0),
-              Q.B + r, 2 * r, 2 * rr, np, st);
+              Q.B + r, 2 * r, 2 * rr, np, qs);
     }
+    if (cudaEventRecord(h->ev_level[l], qs) != cudaSuccess) return HSS_ERR_CUDA;
+    int rc = check_launch();
+    if (rc) return rc;
+  }
+  // main chain
+  for (int l = L; l >= 1; --l) {
+    LevelT<T>& P = f.lv[l];
+    LevelT<T>& Q = f.lv[l - 1];
+    const int b = P.b, n = P.n, c = P.c;
+    const long long br = (long long)b * r, bb = (long long)b * b;
+    const int ldq = 2 * r;
+    const long long sq = 4 * rr;
+    if (cudaStreamWaitEvent(st, h->ev_level[l], 0) != cudaSuccess) return HSS_ERR_CUDA;
     // (b) diagonal product Â = Qᵀ A Q with Q = I - V T Vᵀ, in the symmetric
     // compact-WY form Â = A - Y'Vᵀ - V Y'ᵀ, Y' = A V T - ½ V Tᵀ Vᵀ A V T
     const T* Ain = (l == L) ? f.D : P.A;
@@ -352,8 +382,8 @@ int factor_levels(hss_s* h, Factor<T>& f, cudaStream_t st) {
     // (c) partial Cholesky + (d, second half) Schur complements into the parent
     {
       Launch k(h, HSS_K_PCHOL, pchol_flops(b, c) * n, st, sizeof(T) == 4);
-      HSS_TRY(launch_pchol<T>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1), l, 0,
-                      h->status, n, st));
+      HSS_TRY(launch_pchol<T>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1),
+                              l, 0, h->status, n, st));
     }
     int rc = check_launch();
     if (rc) return rc;
@@ -366,7 +396,7 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
   cudaMemsetAsync(h->status, 0, 8 * sizeof(int), st);
   double* root = nullptr;
   if (prec == HSS_FP64) {
-    int rc = factor_levels<double>(h, h->f64, st);
+    int rc = factor_levels<double>(h, h->f64, h->zq64, st);
     if (rc) return rc;
     root = h->f64.lv[0].A;
   } else {
@@ -387,7 +417,7 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
       Launch k(h, HSS_K_OTHER, 0.0, st);
       launch_f64_to_f32(h->S, f.Sc, h->ssz, st);
     }
-    int rc = factor_levels<float>(h, f, st);
+    int rc = factor_levels<float>(h, f, h->zq32, st);
     if (rc) return rc;
     {   // the root block goes to FP64 for the root Cholesky
       Launch k(h, HSS_K_OTHER, 0.0, st);
@@ -650,6 +680,15 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
     delete h;
     return HSS_ERR_CUDA;
   }
+  h->ev_level.assign(L + 1, nullptr);
+  e = cudaStreamCreateWithFlags(&h->qstream, cudaStreamNonBlocking);
+  e = e ? e : cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+  for (int l = 1; l <= L && e == cudaSuccess; ++l)
+    e = cudaEventCreateWithFlags(&h->ev_level[l], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    hss_destroy(h);
+    return HSS_ERR_CUDA;
+  }
   *out = h;
   return HSS_OK;
 }
@@ -660,6 +699,11 @@ void hss_destroy(hss_t h) {
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
   clear_trace(h);
+  if (h->qstream) cudaStreamSynchronize(h->qstream);
+  for (cudaEvent_t ev : h->ev_level)
+    if (ev) cudaEventDestroy(ev);
+  if (h->ev_start) cudaEventDestroy(h->ev_start);
+  if (h->qstream) cudaStreamDestroy(h->qstream);
   cudaFree(h->arena);
   if (h->f32.arena) cudaFree(h->f32.arena);
   cudaSetDevice(cur);
