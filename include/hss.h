@@ -213,6 +213,42 @@ int hss_launch_count(hss_t h, int64_t* out);
 /* Free the object and its device memory. NULL is ignored. */
 void hss_destroy(hss_t h);
 
+/* ---- batches of independent HSS matrices (FP64) ------------------------------
+ * Many matrices of uneven order, leaf size, rank and depth factored and solved
+ * together; each step of Alg. 2 runs as one launch per (leaf, rank) group and
+ * tree height for all matrices of the group (the "Batching" of uneven problems;
+ * the paper factors one matrix at a time).  Matrices with equal (leaf, rank)
+ * share launches whatever their depth: per group the level arrays are
+ * concatenated by height above the leaves, deepest matrices first, so the
+ * nodes of every height form one uniform batch. */
+typedef struct hss_batch_s* hss_batch_t;
+
+/* Create a batch of `count` matrices: shapes[i] and the generators D[i], U[i],
+ * E[i], S[i] of matrix i as HOST pointers in the packed layout of hss_create
+ * (E[i] may be NULL when levels = 1).  Copies them; the caller keeps ownership.
+ * Synchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+int hss_batch_create(int32_t count, const hss_shape* shapes, const double* const* D,
+                     const double* const* U, const double* const* E, const double* const* S,
+                     hss_batch_t* out);
+
+/* Factor every matrix (Alg. 2, FP64; opt may be NULL, precision must be FP64).
+ * Asynchronous on `stream` (the groups run on internal streams joined to it). */
+int hss_batch_factorize(hss_batch_t b, const hss_options* opt, void* stream);
+
+/* Solve A_i x_i = b_i for every matrix: b[i], x[i] are device pointers to
+ * n_i x nrhs column-major blocks with leading dimension n_i (x[i] may equal b[i]);
+ * the arrays b and x are host arrays of `count` pointers.  Returns after the
+ * work is queued and the pointer tables are consumed (it synchronizes `stream`
+ * once per 16 right-hand-side columns).  Errors: INVALID_ARG, NOT_FACTORIZED, CUDA. */
+int hss_batch_solve(hss_batch_t b, const double* const* bvec, double* const* x, int32_t nrhs,
+                    void* stream);
+
+/* log det of every matrix into out[0 .. count-1] (host).  Synchronizes the
+ * device.  Errors: NOT_FACTORIZED, NOT_SPD (first failure of any matrix). */
+int hss_batch_logdet(hss_batch_t b, double* out);
+
+void hss_batch_destroy(hss_batch_t b);
+
 /* Static string naming a return code. */
 const char* hss_strerror(int code);
 

@@ -52,6 +52,13 @@ SIGNATURES = {
     "hss_matvec_noalloc": (_c_int, [ctypes.POINTER(Shape), _p, _p, _p, _p, _p, _p, ctypes.c_int32,
                                     ctypes.c_int32, _p]),
     "hss_destroy": (None, [_p]),
+    "hss_batch_create": (_c_int, [ctypes.c_int32, ctypes.POINTER(Shape), ctypes.POINTER(_p),
+                                  ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p),
+                                  ctypes.POINTER(_p)]),
+    "hss_batch_factorize": (_c_int, [_p, ctypes.POINTER(Options), _p]),
+    "hss_batch_solve": (_c_int, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.c_int32, _p]),
+    "hss_batch_logdet": (_c_int, [_p, ctypes.POINTER(_c_double)]),
+    "hss_batch_destroy": (None, [_p]),
     "hss_strerror": (ctypes.c_char_p, [_c_int]),
 }
 
@@ -261,3 +268,58 @@ def matvec_noalloc(shape, D, U, E, S, x, y, stream=None):
                                      S.data_ptr(), xp, yp, nrhs, ld, _stream_ptr(stream)),
            "hss_matvec_noalloc")
     return y
+
+
+class HSSBatch:
+    """Many device-resident HSS matrices of uneven shapes, factored and solved
+    together (hss_batch_*)."""
+
+    def __init__(self, mats):
+        lib = load()
+        self.count = len(mats)
+        self.n = [h.n for h in mats]
+        shapes = (Shape * self.count)(*[Shape(h.n, h.leaf, h.rank, h.levels) for h in mats])
+        self._keep = [packed_generators(h) for h in mats]
+        arr = lambda k: (_p * self.count)(*[a[k].ctypes.data for a in self._keep])
+        out = _p()
+        _check(lib.hss_batch_create(self.count, shapes, arr(0), arr(1), arr(2), arr(3),
+                                    ctypes.byref(out)), "hss_batch_create")
+        self._h = out
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hss_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factorize(self, stream=None):
+        opt = Options(HSS_FP64, 0, 0.0)
+        _check(load().hss_batch_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
+               "hss_batch_factorize")
+
+    def solve(self, bs, xs=None, stream=None):
+        """bs: list of column-major float64 CUDA tensors (n_i x nrhs, ld = n_i)."""
+        import torch
+        if xs is None:
+            xs = [torch.empty((b.shape[1], b.shape[0]), dtype=b.dtype, device=b.device).t()
+                  for b in bs]
+        nrhs = bs[0].shape[1]
+        for b, x, n in zip(bs, xs, self.n):
+            if b.shape != (n, nrhs) or x.shape != (n, nrhs) or b.stride(0) != 1 or x.stride(0) != 1:
+                raise ValueError("each b_i, x_i must be n_i x nrhs column-major")
+        bp = (_p * self.count)(*[b.data_ptr() for b in bs])
+        xp = (_p * self.count)(*[x.data_ptr() for x in xs])
+        _check(load().hss_batch_solve(self._h, bp, xp, nrhs, _stream_ptr(stream)),
+               "hss_batch_solve")
+        return xs
+
+    def logdet(self):
+        out = (ctypes.c_double * self.count)()
+        _check(load().hss_batch_logdet(self._h, out), "hss_batch_logdet")
+        return np.array(out[:])

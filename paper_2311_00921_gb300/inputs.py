@@ -94,12 +94,16 @@ def make_points(w: Workload, rng: np.random.Generator) -> np.ndarray:
         g = rng.standard_normal((n, 3))
         return g / np.linalg.norm(g, axis=1, keepdims=True)
     if w.geometry == "grid2d":
-        side = int(round(math.sqrt(n)))
-        if side * side != n:
-            raise ValueError("grid2d needs a square point count")
-        i, j = np.meshgrid(np.arange(side), np.arange(side), indexing="ij")
-        jit = rng.uniform(-0.25, 0.25, size=(2, side, side))
-        p = np.stack([(i + 0.5 + jit[0]) / side, (j + 0.5 + jit[1]) / side], -1)
+        # sx x sy jittered grid of the unit square (sx = sy when n is a square)
+        sx = int(round(math.sqrt(n)))
+        if sx * sx != n:
+            sx = 1 << int(math.ceil(math.log2(n) / 2))
+        sy = n // sx
+        if sx * sy != n:
+            raise ValueError("grid2d needs n = sx * sy")
+        i, j = np.meshgrid(np.arange(sx), np.arange(sy), indexing="ij")
+        jit = rng.uniform(-0.25, 0.25, size=(2, sx, sy))
+        p = np.stack([(i + 0.5 + jit[0]) / sx, (j + 0.5 + jit[1]) / sy], -1)
         return p.reshape(n, 2)
     if w.geometry == "line":
         return np.sort(rng.random((n, 1)), axis=0)
@@ -479,3 +483,27 @@ def cached_build(w: Workload, cache_dir: Optional[str], **kw) -> HSSMatrix:
         np.savez(tmp, **arrs)
         os.replace(tmp, path)
     return h
+
+
+def batch_workloads(count: int, seed: int = 1003, n_min: int = 4096, n_max: int = 65536):
+    """The batched uneven workload: `count` matrices, N log-uniform in
+    [n_min, n_max] rounded to leaf * 2^L (a uniform tree per matrix), leaf drawn
+    from {128, 256, 512}, rank from {32, 64, 128}, kernel half 1/(d + 1e-3) on
+    the unit cube (+ N^(1/3) I), half exp(-d / 0.1) on a jittered 2-D grid
+    (+ 1e-4 I); one right-hand side each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        leaf = int(rng.choice([128, 256, 512]))
+        rank = int(rng.choice([32, 64, 128]))
+        n_target = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        L = max(1, int(round(math.log2(n_target / leaf))))
+        n = leaf * 2 ** L
+        if rng.random() < 0.5:
+            w = Workload(f"batch{i}_cube_inv", n, leaf, rank, "cube", "inv", 0.0,
+                         round(n ** (1.0 / 3.0), 6), 1, seed * 1000 + i)
+        else:
+            w = Workload(f"batch{i}_grid_exp", n, leaf, rank, "grid2d", "exp", 0.1, 1e-4, 1,
+                         seed * 1000 + i)
+        out.append(w)
+    return out
