@@ -440,6 +440,70 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Batched uneven workload: `--batch` matrices of the batched-workload shape
+    distribution (N log-uniform in [4096, 65536] rounded to leaf x 2^L, leaf in
+    {128, 256, 512}, rank in {32, 64, 128}, one right-hand side each), factored
+    and solved by the batch path (plain and CUDA-graph replay) and by a loop of
+    single-matrix calls.  The generators are random (SPD by a diagonal shift)
+    with those shapes: values do not change the work."""
+    import torch
+    from paper_2311_00921_gb300 import hss, inputs as I
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ws = I.batch_workloads(args.batch, seed=1003)
+    mats = [I.random_hss(w.levels, w.leaf, w.rank, seed=w.seed, orthonormal=False,
+                         fast_bound=True) for w in ws]
+    fl = sum(factor_flops(w.levels, w.leaf, w.rank) + solve_flops(w.levels, w.leaf, w.rank, 1)
+             for w in ws)
+    bs = [hss.colmajor(I.rhs(h.n, 1, i)) for i, h in enumerate(mats)]
+    out = {}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    bt = hss.HSSBatch(mats)
+    xs = [torch.empty_like(b) for b in bs]
+    out["batch_ms"] = timed(lambda: (bt.factorize(), bt.solve(bs, xs)))
+    bt.use_graph(True)
+    out["batch_graph_ms"] = timed(lambda: (bt.factorize(), bt.solve(bs, xs)))
+    lds = bt.logdet()
+    del bt
+    torch.cuda.empty_cache()
+    objs = [hss.HSS(h) for h in mats]
+
+    def loop():
+        for o, b, x in zip(objs, bs, xs):
+            o.factorize("fp64")
+            o.solve(b, x)
+    out["loop_ms"] = timed(loop)
+    lds_loop = np.array([o.logdet() for o in objs])
+    ms = min(out["batch_ms"], out["batch_graph_ms"])
+    res = {"metric": "batched uneven HSS-ULV factor+solve, 256 matrices (FP64)",
+           "value": fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (random generators with the batched workload's shapes)",
+           "config": {"workload": f"batch{args.batch}_uneven", "matrices": args.batch,
+                      "total_n": int(sum(w.n for w in ws)),
+                      "groups": len({(w.leaf, w.rank) for w in ws})},
+           "batch_ms": out["batch_ms"], "batch_graph_ms": out["batch_graph_ms"],
+           "loop_of_single_calls_ms": out["loop_ms"],
+           "speedup_vs_loop": out["loop_ms"] / ms,
+           "max_logdet_rel_diff_vs_loop": float(np.max(np.abs(lds - lds_loop) /
+                                                       np.abs(lds_loop)))}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def run_e2e(args, h, w, b_host, prec, fl_step, world, dist):
     """One user call sequence per step from pinned host memory: create the object
     (H2D of the generators), factor, upload b, solve, read x back, destroy."""
@@ -504,6 +568,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "tf32", "bf16", "fp32"],
                     help="factor arithmetic; non-fp64 modes refine in FP64 to 1e-12")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="run the batched uneven workload with this many matrices instead")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--n", type=int, default=0,
                     help="scale the workload to this order (same leaf, rank, kernel)")
@@ -514,6 +580,8 @@ def main():
         raise SystemExit("at least 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -235,6 +235,12 @@ int hss_batch_create(int32_t count, const hss_shape* shapes, const double* const
  * Asynchronous on `stream` (the groups run on internal streams joined to it). */
 int hss_batch_factorize(hss_batch_t b, const hss_options* opt, void* stream);
 
+/* With enable = 1, later hss_batch_factorize calls run from a CUDA graph: the
+ * first such call runs the factorization once, then captures its launches (on
+ * an internal stream) into a graph; every call after that replays the graph,
+ * ordered after earlier work on `stream` and before later work on it. */
+int hss_batch_set_graph(hss_batch_t b, int32_t enable);
+
 /* Solve A_i x_i = b_i for every matrix: b[i], x[i] are device pointers to
  * n_i x nrhs column-major blocks with leading dimension n_i (x[i] may equal b[i]);
  * the arrays b and x are host arrays of `count` pointers.  Returns after the

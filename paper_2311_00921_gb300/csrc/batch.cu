@@ -71,6 +71,11 @@ struct hss_batch_s {
   int factorized = 0;
   cudaEvent_t ev_join = nullptr;
   std::vector<cudaEvent_t> ev_group;
+  // optional CUDA graph of the whole factorization (captured on cap_stream)
+  int use_graph = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaEvent_t ev_cap_in = nullptr, ev_cap_out = nullptr;
 };
 
 namespace {
@@ -353,6 +358,15 @@ int fork_join(hss_batch_s* bt, cudaStream_t st, F fn) {
   return rc;
 }
 
+int enqueue_factorize(hss_batch_s* bt, cudaStream_t st) {
+  if (cudaMemsetAsync(bt->status, 0, 8 * sizeof(int), st) != cudaSuccess) return HSS_ERR_CUDA;
+  int rc = fork_join(bt, st, [&](Group& g) { return factor_group(bt, g); });
+  if (rc) return rc;
+  batch_logdet_kernel<<<bt->count, 256, 0, st>>>(bt->ldp_all, bt->ranges, bt->range_start,
+                                                 bt->logdet);
+  return cudaGetLastError() == cudaSuccess ? HSS_OK : HSS_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -520,8 +534,19 @@ void hss_batch_destroy(hss_batch_t bt) {
     if (g.qs) cudaStreamDestroy(g.qs);
   }
   if (bt->ev_join) cudaEventDestroy(bt->ev_join);
+  if (bt->cap_stream) cudaStreamSynchronize(bt->cap_stream);
+  if (bt->graph_exec) cudaGraphExecDestroy(bt->graph_exec);
+  if (bt->ev_cap_in) cudaEventDestroy(bt->ev_cap_in);
+  if (bt->ev_cap_out) cudaEventDestroy(bt->ev_cap_out);
+  if (bt->cap_stream) cudaStreamDestroy(bt->cap_stream);
   cudaFree(bt->arena);
   delete bt;
+}
+
+int hss_batch_set_graph(hss_batch_t bt, int32_t enable) {
+  if (!bt) return HSS_ERR_INVALID_ARG;
+  bt->use_graph = enable ? 1 : 0;
+  return HSS_OK;
 }
 
 int hss_batch_factorize(hss_batch_t bt, const hss_options* opt, void* stream) {
@@ -529,12 +554,48 @@ int hss_batch_factorize(hss_batch_t bt, const hss_options* opt, void* stream) {
   if (opt && opt->precision != HSS_FP64) return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   bt->factorized = 0;
-  if (cudaMemsetAsync(bt->status, 0, 8 * sizeof(int), st) != cudaSuccess) return HSS_ERR_CUDA;
-  int rc = fork_join(bt, st, [&](Group& g) { return factor_group(bt, g); });
-  if (rc) return rc;
-  batch_logdet_kernel<<<bt->count, 256, 0, st>>>(bt->ldp_all, bt->ranges, bt->range_start,
-                                                 bt->logdet);
-  if (cudaGetLastError() != cudaSuccess) return HSS_ERR_CUDA;
+  if (!bt->use_graph) {
+    int rc = enqueue_factorize(bt, st);
+    if (rc) return rc;
+    bt->factorized = 1;
+    return HSS_OK;
+  }
+  if (!bt->graph_exec) {
+    // one plain run first (kernel attributes, module loading), then capture the
+    // same launches on the object's own stream
+    int rc = enqueue_factorize(bt, st);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    if (!bt->cap_stream) {
+      e = e ? e : cudaStreamCreateWithFlags(&bt->cap_stream, cudaStreamNonBlocking);
+      e = e ? e : cudaEventCreateWithFlags(&bt->ev_cap_in, cudaEventDisableTiming);
+      e = e ? e : cudaEventCreateWithFlags(&bt->ev_cap_out, cudaEventDisableTiming);
+      if (e) return HSS_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return HSS_ERR_CUDA;
+    rc = enqueue_factorize(bt, bt->cap_stream);
+    e = cudaStreamEndCapture(bt->cap_stream, &graph);
+    if (rc || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc ? rc : HSS_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&bt->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      bt->graph_exec = nullptr;
+      return HSS_ERR_CUDA;
+    }
+  }
+  cudaError_t e = cudaEventRecord(bt->ev_cap_in, st);
+  e = e ? e : cudaStreamWaitEvent(bt->cap_stream, bt->ev_cap_in, 0);
+  e = e ? e : cudaGraphLaunch(bt->graph_exec, bt->cap_stream);
+  e = e ? e : cudaEventRecord(bt->ev_cap_out, bt->cap_stream);
+  e = e ? e : cudaStreamWaitEvent(st, bt->ev_cap_out, 0);
+  if (e != cudaSuccess) return HSS_ERR_CUDA;
   bt->factorized = 1;
   return HSS_OK;
 }

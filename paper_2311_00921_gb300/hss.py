@@ -59,6 +59,7 @@ SIGNATURES = {
     "hss_batch_solve": (_c_int, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.c_int32, _p]),
     "hss_batch_logdet": (_c_int, [_p, ctypes.POINTER(_c_double)]),
     "hss_batch_destroy": (None, [_p]),
+    "hss_batch_set_graph": (_c_int, [_p, ctypes.c_int32]),
     "hss_strerror": (ctypes.c_char_p, [_c_int]),
 }
 
@@ -302,6 +303,9 @@ class HSSBatch:
         opt = Options(HSS_FP64, 0, 0.0)
         _check(load().hss_batch_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_batch_factorize")
+
+    def use_graph(self, enable=True):
+        _check(load().hss_batch_set_graph(self._h, 1 if enable else 0), "hss_batch_set_graph")
 
     def solve(self, bs, xs=None, stream=None):
         """bs: list of column-major float64 CUDA tensors (n_i x nrhs, ld = n_i)."""

@@ -411,7 +411,8 @@ def kernel_matrix(w: Workload, pts: np.ndarray) -> np.ndarray:
 
 
 def random_hss(levels: int, leaf: int, rank: int, seed: int, *,
-               shift: float = None, orthonormal: bool = True) -> HSSMatrix:
+               shift: float = None, orthonormal: bool = True,
+               fast_bound: bool = False) -> HSSMatrix:
     """Random-generator HSS matrix (no kernel): SPD by a diagonal shift.
 
     Bases are random Gaussian (orthonormalised if requested), transfers and
@@ -431,12 +432,14 @@ def random_hss(levels: int, leaf: int, rank: int, seed: int, *,
          for l in range(1, L + 1)}
     if shift is None:
         # ||off-diagonal part|| <= sum_l max_k ||S_lk|| * (max nested-basis norm)^2
-        nb = max(np.linalg.norm(u, 2) for u in U)
+        # (fast_bound: Frobenius norms, cheap upper bounds of the 2-norms)
+        nrm = (lambda a: np.linalg.norm(a)) if fast_bound else (lambda a: np.linalg.norm(a, 2))
+        nb = max(nrm(u) for u in U)
         bound = 0.0
         for l in range(L, 0, -1):
-            bound += max(np.linalg.norm(s, 2) for s in S[l]) * nb * nb
+            bound += max(nrm(s) for s in S[l]) * nb * nb
             if l > 1:
-                nb *= max(np.linalg.norm(e, 2) for e in E[l - 1])
+                nb *= max(nrm(e) for e in E[l - 1])
         shift = 2.0 * bound + 1.0
     D = []
     for _ in range(2 ** L):

@@ -65,3 +65,20 @@ def test_batch_workload_family_reduced():
     ws = I.batch_workloads(6, seed=7, n_min=512, n_max=4096)
     mats = [I.build_hss(w) for w in ws]
     check_batch(mats, 1, 3)
+
+
+def test_batch_graph_replay_matches_plain():
+    mats = [I.random_hss(L, 64, 16, seed=30 + L) for L in (2, 3, 1, 3)]
+    plain, graph = hss.HSSBatch(mats), hss.HSSBatch(mats)
+    plain.factorize()
+    graph.use_graph(True)
+    bs = [hss.colmajor(I.rhs(h.n, 2, 5 + i)) for i, h in enumerate(mats)]
+    ref_ld = plain.logdet()
+    ref_x = [x.cpu().numpy() for x in plain.solve(bs)]
+    for _ in range(3):            # capture on the first call, replay afterwards
+        graph.factorize()
+        lds = graph.logdet()
+        xs = graph.solve(bs)
+        assert np.array_equal(lds, ref_ld)
+        for x, xr in zip(xs, ref_x):
+            assert np.array_equal(x.cpu().numpy(), xr)
