@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kMaxCols = 32;      // right-hand-side columns per matvec pass
 constexpr int kSolveCols = 16;    // columns per triangular-sweep / refinement pass
+constexpr int kRootPanels = 16;   // log-det slots of the blocked root Cholesky (2r <= 512)
 
 template <typename T>
 struct LevelT {
@@ -63,6 +64,9 @@ struct hss_s {
   std::vector<double*> xh, yh;         // matvec up / down sweep per level: (2^l r) x kMaxCols
   double* R0 = nullptr;                // FP64 root block of a mixed factor (2r x 2r)
   double* root_vec = nullptr;          // FP64 root vector of a mixed solve (2r x kSolveCols)
+  double* root_vec2 = nullptr;
+  double* A0inv = nullptr;             // FP64 inverse of the root block (mixed solves)
+  int a0inv_valid = 0;
   double* rbuf = nullptr;              // n x kSolveCols residual
   double* bbuf = nullptr;              // n x kSolveCols copy of b (x aliasing b)
   double* norms = nullptr;             // 4 x kSolveCols: |b|, 1/|b|, |r|, 1/|r|
@@ -176,11 +180,13 @@ size_t layout_main(hss_s* h, char* base) {
   }
   h->zq64 = bp.take<double>((size_t)nL * r * r);
   h->R0 = bp.take<double>((size_t)4 * r * r);
+  h->A0inv = bp.take<double>((size_t)4 * r * r);
   h->root_vec = bp.take<double>((size_t)2 * r * kSolveCols);
+  h->root_vec2 = bp.take<double>((size_t)2 * r * kSolveCols);
   h->rbuf = bp.take<double>((size_t)h->n * kSolveCols);
   h->bbuf = bp.take<double>((size_t)h->n * kSolveCols);
   h->norms = bp.take<double>(4 * kSolveCols);
-  h->logdet_part = bp.take<double>((size_t)(2 * nL - 1));
+  h->logdet_part = bp.take<double>((size_t)(2 * nL - 1) + kRootPanels);
   h->logdet_val = bp.take<double>(1);
   h->status = bp.take<int>(8);
   return bp.off + 256;
@@ -391,6 +397,32 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st) {
   return HSS_OK;
 }
 
+// Blocked right-looking Cholesky of the FP64 root block (Alg. 2 line 6): a
+// one-CTA panel step (diagonal block and the rows below it) and a many-CTA
+// GEMM for the trailing update, so the 2r x 2r root is not bound to one SM.
+int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
+  double* slots = h->logdet_part + ((2LL << h->L) - 1);
+  if (cudaMemsetAsync(slots, 0, kRootPanels * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(h->logdet_part, 0, sizeof(double), st) != cudaSuccess)
+    return HSS_ERR_CUDA;
+  constexpr int KB = 32;
+  for (int k0 = 0, p = 0; k0 < b0; k0 += KB, ++p) {
+    const int kb = std::min(KB, b0 - k0), rows = b0 - k0;
+    double* Mk = R + k0 + (long long)k0 * b0;
+    {
+      Launch k(h, HSS_K_PCHOL, (double)kb * kb * kb / 3.0 + (double)(rows - kb) * kb * kb, st);
+      HSS_TRY(launch_chol_panel<double>(Mk, b0, rows, kb, slots + p, 0, k0, h->status, st));
+    }
+    const int nt = rows - kb;
+    if (nt > 0) {
+      double* P = Mk + kb;   // rows below the panel
+      gemm<double>(h, false, true, nt, nt, kb, -1.0, P, b0, 0, P, b0, 0, 1.0,
+                   R + (k0 + kb) + (long long)(k0 + kb) * b0, b0, 0, 1, st);
+    }
+  }
+  return check_launch();
+}
+
 int factorize(hss_s* h, int prec, cudaStream_t st) {
   const int L = h->L, r = h->rank;
   cudaMemsetAsync(h->status, 0, 8 * sizeof(int), st);
@@ -427,14 +459,34 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
   }
   // root Cholesky (Alg. 2 line 6), FP64 in every mode
   const int b0 = 2 * r;
-  {
-    Launch k(h, HSS_K_PCHOL, pchol_flops(b0, b0), st);
-    HSS_TRY(launch_pchol<double>(root, b0, (long long)b0 * b0, b0, b0, nullptr, 0, 0, h->logdet_part, 0,
-                         0, h->status, 1, st));
-  }
+  int rc = root_cholesky(h, root, b0, st);
+  if (rc) return rc;
   {
     Launch k(h, HSS_K_OTHER, (double)((2LL << L) - 1), st);
-    launch_logdet_reduce(h->logdet_part, (int)((2LL << L) - 1), h->logdet_val, st);
+    launch_logdet_reduce(h->logdet_part, (int)((2LL << L) - 1) + kRootPanels, h->logdet_val, st);
+  }
+  // mixed modes: the root solve of every refinement pass multiplies by the FP64
+  // inverse of the root block, formed here from its Cholesky factor with the
+  // triangular sweeps run on the identity, 16 columns per CTA
+  h->a0inv_valid = 0;
+  if (prec != HSS_FP64 && b0 % kSolveCols == 0) {
+    {
+      Launch k(h, HSS_K_OTHER, 0.0, st);
+      launch_eye(h->A0inv, b0, st);
+    }
+    const int chunks = b0 / kSolveCols;
+    const long long sx = (long long)kSolveCols * b0;
+    {
+      Launch k(h, HSS_K_TRSV_FWD, trsv_flops(b0, b0, b0), st);
+      HSS_TRY(launch_trsv_fwd<double>(root, b0, 0, b0, b0, h->A0inv, b0, sx, kSolveCols, nullptr,
+                                      0, 0, chunks, st));
+    }
+    {
+      Launch k(h, HSS_K_TRSV_BWD, trsv_flops(b0, b0, b0), st);
+      HSS_TRY(launch_trsv_bwd<double>(root, b0, 0, b0, b0, h->A0inv, b0, sx, kSolveCols, nullptr,
+                                      0, 0, chunks, st));
+    }
+    h->a0inv_valid = 1;
   }
   return check_launch();
 }
@@ -466,13 +518,19 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     Launch k(h, HSS_K_OTHER, 0.0, st);
     launch_f32_to_f64(reinterpret_cast<const float*>(f.lv[0].yv), rv, (long long)b0 * nc, st);
   }
-  {
-    Launch k(h, HSS_K_TRSV_FWD, trsv_flops(b0, b0, nc), st);
-    HSS_TRY(launch_trsv_fwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st));
-  }
-  {
-    Launch k(h, HSS_K_TRSV_BWD, trsv_flops(b0, b0, nc), st);
-    HSS_TRY(launch_trsv_bwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st));
+  if (sizeof(T) != sizeof(double) && h->a0inv_valid) {
+    gemm<double>(h, false, false, b0, nc, b0, 1.0, h->A0inv, b0, 0, rv, b0, 0, 0.0, h->root_vec2,
+                 b0, 0, 1, st);
+    rv = h->root_vec2;
+  } else {
+    {
+      Launch k(h, HSS_K_TRSV_FWD, trsv_flops(b0, b0, nc), st);
+      HSS_TRY(launch_trsv_fwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st));
+    }
+    {
+      Launch k(h, HSS_K_TRSV_BWD, trsv_flops(b0, b0, nc), st);
+      HSS_TRY(launch_trsv_bwd<double>(rootA, b0, 0, b0, b0, rv, b0, 0, nc, nullptr, 0, 0, 1, st));
+    }
   }
   if (sizeof(T) != sizeof(double)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);

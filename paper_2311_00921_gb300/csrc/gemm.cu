@@ -225,11 +225,90 @@ gemm_n16_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, 
   }
 }
 
+// n <= 16 columns, few output tiles: CTA = 32 rows x 16 columns, 64 threads
+// with a 2 x 4 micro-tile each (rows lane + 16 p of the half-warp pair,
+// columns (warp * 2 + half) + 4 q).  Used when a launch would not fill the
+// GPU: a 128-row tile of an FP64 product with k = 256 takes ~0.1 ms on one SM,
+// so the top levels of the tree need the rows spread over more SMs.
+template <typename T, bool TA, bool TB, bool BETA>
+__global__ void __launch_bounds__(64)
+gemm_n16_small_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda,
+                      long long sA, const T* __restrict__ B, int ldb, long long sB, T beta, T* C,
+                      int ldc, long long sC) {
+  constexpr int SBM = 32, SBK = 32, SNT = 64;
+  __shared__ T As[SBK][SBM + 1];
+  __shared__ T Bs[SBK][16 + 1];
+  const long long bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int i0 = blockIdx.x * SBM;
+  const int tid = threadIdx.x;
+  const int rl = tid & 15, cg = tid >> 4;   // row lane 0..15, column group 0..3
+  T acc[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int k0 = 0; k0 < k; k0 += SBK) {
+    for (int e = tid; e < SBM * SBK; e += SNT) {
+      int i, kk;
+      if (!TA) { i = e % SBM; kk = e / SBM; } else { kk = e % SBK; i = e / SBK; }
+      const int gi = i0 + i, gk = k0 + kk;
+      T v = T(0);
+      if (gi < m && gk < k) v = TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
+      As[kk][i] = v;
+    }
+    for (int e = tid; e < 16 * SBK; e += SNT) {
+      int j, kk;
+      if (!TB) { kk = e % SBK; j = e / SBK; } else { j = e % 16; kk = e / 16; }
+      const int gk = k0 + kk;
+      T v = T(0);
+      if (j < n && gk < k) v = TB ? B[j + (long long)gk * ldb] : B[gk + (long long)j * ldb];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < SBK; ++kk) {
+      const T a0 = As[kk][rl], a1 = As[kk][rl + 16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T bv = Bs[kk][cg + 4 * q];
+        acc[0][q] = fma(a0, bv, acc[0][q]);
+        acc[1][q] = fma(a1, bv, acc[1][q]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gj = cg + 4 * q;
+    if (gj >= n) continue;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int gi = i0 + rl + 16 * p;
+      if (gi >= m) continue;
+      T* c = C + gi + (long long)gj * ldc;
+      *c = BETA ? fma(alpha, acc[p][q], beta * *c) : alpha * acc[p][q];
+    }
+  }
+}
+
 template <typename T, bool TA, bool TB>
 void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA, const T* B,
                  int ldb, long long sB, T beta, T* C, int ldc, long long sC, int batch,
                  cudaStream_t st) {
   const bool useb = beta != T(0);
+  if (n > 4 && n <= 16 && (long long)((m + 127) / 128) * batch < 152) {
+    dim3 g((m + 31) / 32, 1, batch);
+    if (useb)
+      gemm_n16_small_kernel<T, TA, TB, true><<<g, 64, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb,
+                                                              sB, beta, C, ldc, sC);
+    else
+      gemm_n16_small_kernel<T, TA, TB, false><<<g, 64, 0, st>>>(m, n, k, alpha, A, lda, sA, B,
+                                                               ldb, sB, beta, C, ldc, sC);
+    return;
+  }
   if (n > 4 && n <= 16) {
     dim3 g((m + 127) / 128, 1, batch);
     if (useb)

@@ -67,6 +67,12 @@ __global__ void col_norms_kernel(const double* __restrict__ v, int ld, int m, do
   }
 }
 
+__global__ void eye_kernel(double* a, int n) {
+  for (long long e = blockIdx.x * (long long)NT + threadIdx.x; e < (long long)n * n;
+       e += (long long)gridDim.x * NT)
+    a[e] = (e % n == e / n) ? 1.0 : 0.0;
+}
+
 int grid_for(long long n) {
   long long g = (n + NT - 1) / NT;
   return (int)(g < 152 * 16 ? (g < 1 ? 1 : g) : 152 * 16);
@@ -102,4 +108,8 @@ void launch_residual(const double* b, int ldb, double* r, int ldr, int m, int nc
 void launch_col_norms(const double* v, int ld, int m, int nc, double* norms, double* inv,
                       cudaStream_t st) {
   col_norms_kernel<<<nc, 1024, 0, st>>>(v, ld, m, norms, inv);
+}
+
+void launch_eye(double* a, int n, cudaStream_t st) {
+  eye_kernel<<<grid_for((long long)n * n), NT, 0, st>>>(a, n);
 }

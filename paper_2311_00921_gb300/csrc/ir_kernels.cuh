@@ -13,3 +13,4 @@ void launch_cols_update(double* x, int ldx, const float* d, int ldd, int m, int 
 void launch_residual(const double* b, int ldb, double* r, int ldr, int m, int nc, cudaStream_t st);
 void launch_col_norms(const double* v, int ld, int m, int nc, double* norms, double* inv,
                       cudaStream_t st);
+void launch_eye(double* a, int n, cudaStream_t st);   // a = I (n x n, column-major)

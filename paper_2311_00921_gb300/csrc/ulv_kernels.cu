@@ -309,7 +309,7 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
 template <typename T>
 __global__ void __launch_bounds__(NT)
 pchol_kernel(T* Mb, int ldm, long long sM, int b, int c, T* PA, int ldpa, long long sPA,
-             double* logdet_part, int level, int node0, int* status) {
+             double* logdet_part, int level, int node0, int* status, int panel_only) {
   extern __shared__ unsigned char smem_raw[];
   T* P = reinterpret_cast<T*>(smem_raw);   // panel: b rows x NB, column-major ld = b
   __shared__ int fail;
@@ -385,10 +385,11 @@ pchol_kernel(T* Mb, int ldm, long long sM, int b, int c, T* PA, int ldpa, long l
       const int i = e % n1, jj = e / n1;
       if (i >= jj) M[(k0 + i) + (long long)(k0 + jj) * ldm] = P[i + jj * b];
     }
-    // trailing update of the lower triangle, rows/cols >= k0 + kb
+    // trailing update of the lower triangle, rows/cols >= k0 + kb (left to the
+    // caller in panel_only mode, where c is the panel width)
     const int base = kb;   // panel row of the first trailing index
     const int n2 = n1 - kb;
-    if (n2 > 0) {
+    if (n2 > 0 && !panel_only) {
       const int nt = (n2 + 63) / 64;
       const int tx = tid & 15, ty = tid >> 4;
       for (int tp = 0; tp < nt * (nt + 1) / 2; ++tp) {
@@ -645,7 +646,18 @@ cudaError_t launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int l
   const size_t sm = pchol_smem<T>(b);
   if (!smem_opt_in(pchol_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
   pchol_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, PA, ldpa, sPA, logdet_part, level,
-                                         node0, status);
+                                         node0, status, 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_chol_panel(T* M, int ldm, int rows, int kb, double* logdet_slot, int level,
+                              int col0, int* status, cudaStream_t st) {
+  const size_t sm = pchol_smem<T>(rows);
+  if (!smem_opt_in(pchol_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
+  (void)col0;   // failures report the column within the panel
+  pchol_kernel<T><<<1, NT, sm, st>>>(M, ldm, 0, rows, kb, nullptr, 0, 0, logdet_slot, level, 0,
+                                     status, 1);
   return cudaGetLastError();
 }
 
@@ -682,6 +694,8 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
                                           int, T*, int, long long, int, cudaStream_t);            \
   template cudaError_t launch_trsv_bwd<T>(const T*, int, long long, int, int, T*, int, long long, \
                                           int, const T*, int, long long, int, cudaStream_t);      \
-  template size_t ql_smem<T>(int, int);
+  template size_t ql_smem<T>(int, int);                                                          \
+  template cudaError_t launch_chol_panel<T>(T*, int, int, int, double*, int, int, int*,           \
+                                            cudaStream_t);
 INST(double)
 INST(float)

@@ -28,3 +28,10 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
 // dynamic shared memory of the basis-completion kernel for a b x r basis
 template <typename T>
 size_t ql_smem(int b, int r);
+
+// One panel of a blocked Cholesky: factor the kb x kb diagonal block at the
+// top of the rows x rows matrix M (ld ldm) and solve the rows below it; the
+// trailing update is left to the caller.  Writes 2 Σ log diag to *logdet_slot.
+template <typename T>
+cudaError_t launch_chol_panel(T* M, int ldm, int rows, int kb, double* logdet_slot, int level,
+                              int col0, int* status, cudaStream_t st);
