@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kMaxCols = 32;      // right-hand-side columns per matvec pass
 constexpr int kSolveCols = 16;    // columns per triangular-sweep / refinement pass
+constexpr int kPanel = 32;        // columns per blocked-Cholesky panel (the panel kernel's limit)
 constexpr int kRootPanels = 16;   // log-det slots of the blocked root Cholesky (2r <= 512)
 
 template <typename T>
@@ -275,9 +276,9 @@ void gemm(hss_s* h, bool ta, bool tb, int m, int n, int k, T alpha, const T* A, 
 
 // partial Cholesky of the first c of b columns: POTRF c x c, TRSM (b-c) x c,
 // SYRK (b-c) x (b-c) with depth c
-double pchol_flops(int b, int c) {
-  const double r = b - c;
-  return (double)c * c * c / 3.0 + r * c * c + r * (r + 1.0) * c;
+// one Cholesky panel: kb x kb POTRF plus the (rows - kb) x kb TRSM
+double panel_flops(int rows, int kb) {
+  return (double)kb * kb * kb / 3.0 + (double)(rows - kb) * kb * kb;
 }
 
 // triangular sweep of one node: c x c triangle plus the (b-c) x c block
@@ -385,11 +386,30 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st) {
       Launch k(h, HSS_K_SYR2K, 2.0 * r * b * (b + 1.0) * n, st, sizeof(T) == 4);
       syr2k_lower_batched<T>(b, r, Ain, b, bb, f.Y, b, br, P.V, b, br, P.M, b, bb, n, st);
     }
-    // (c) partial Cholesky + (d, second half) Schur complements into the parent
+    // (c) partial Cholesky of the first c columns, blocked over the whole level:
+    // per panel of kPanel columns a per-node panel kernel (diagonal block and
+    // the rows below it) and one SYRK of every node's trailing lower triangle
+    double* slots = h->logdet_part + ((1LL << l) - 1);
+    if (c == 0 && cudaMemsetAsync(slots, 0, sizeof(double) * n, st) != cudaSuccess)
+      return HSS_ERR_CUDA;
+    for (int k0 = 0; k0 < c; k0 += kPanel) {
+      const int kb = std::min(kPanel, c - k0), rows = b - k0, nt = rows - kb;
+      T* Mk = P.M + k0 + (long long)k0 * b;
+      {
+        Launch k(h, HSS_K_PCHOL, panel_flops(rows, kb) * n, st, sizeof(T) == 4);
+        HSS_TRY(launch_chol_panel<T>(Mk, b, bb, rows, kb, slots, l, k0, h->status, n, k0 > 0,
+                                     st));
+      }
+      if (nt > 0) {
+        Launch k(h, HSS_K_SYR2K, (double)nt * (nt + 1.0) * kb * n, st, sizeof(T) == 4);
+        T* Tr = Mk + kb + (long long)kb * b;
+        syrk_lower_batched<T>(nt, kb, Tr, b, bb, Mk + kb, b, bb, Tr, b, bb, n, st);
+      }
+    }
+    // (d, second half) Â^SS into the parents' diagonal blocks
     {
-      Launch k(h, HSS_K_PCHOL, pchol_flops(b, c) * n, st, sizeof(T) == 4);
-      HSS_TRY(launch_pchol<T>(P.M, b, bb, b, c, Q.A, ldq, sq, h->logdet_part + ((1LL << l) - 1),
-                              l, 0, h->status, n, st));
+      Launch k(h, HSS_K_OTHER, 0.0, st, sizeof(T) == 4);
+      HSS_TRY(launch_scatter_ss<T>(P.M, b, bb, c, r, Q.A, ldq, sq, n, st));
     }
     int rc = check_launch();
     if (rc) return rc;
@@ -405,13 +425,13 @@ int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
   if (cudaMemsetAsync(slots, 0, kRootPanels * sizeof(double), st) != cudaSuccess ||
       cudaMemsetAsync(h->logdet_part, 0, sizeof(double), st) != cudaSuccess)
     return HSS_ERR_CUDA;
-  constexpr int KB = 32;
-  for (int k0 = 0, p = 0; k0 < b0; k0 += KB, ++p) {
-    const int kb = std::min(KB, b0 - k0), rows = b0 - k0;
+  for (int k0 = 0, p = 0; k0 < b0; k0 += kPanel, ++p) {
+    const int kb = std::min(kPanel, b0 - k0), rows = b0 - k0;
     double* Mk = R + k0 + (long long)k0 * b0;
     {
-      Launch k(h, HSS_K_PCHOL, (double)kb * kb * kb / 3.0 + (double)(rows - kb) * kb * kb, st);
-      HSS_TRY(launch_chol_panel<double>(Mk, b0, rows, kb, slots + p, 0, k0, h->status, st));
+      Launch k(h, HSS_K_PCHOL, panel_flops(rows, kb), st);
+      HSS_TRY(launch_chol_panel<double>(Mk, b0, 0, rows, kb, slots + p, 0, k0, h->status, 1,
+                                        false, st));
     }
     const int nt = rows - kb;
     if (nt > 0) {

@@ -63,3 +63,8 @@ template <typename T>
 void syr2k_lower_batched(int m, int k, const T* A, int lda, long long sA,
                          const T* P, int ldp, long long sP, const T* Q, int ldq, long long sQ,
                          T* M, int ldm, long long sM, int batch, cudaStream_t st);
+
+// M(i, j) = A(i, j) - sum_k P(i,k) P(j,k) on the lower triangle; A may alias M.
+template <typename T>
+void syrk_lower_batched(int m, int k, const T* A, int lda, long long sA, const T* P, int ldp,
+                        long long sP, T* M, int ldm, long long sM, int batch, cudaStream_t st);

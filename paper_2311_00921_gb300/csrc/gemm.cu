@@ -338,8 +338,9 @@ void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA
                                                         beta, C, ldc, sC);
 }
 
-// lower-triangle tiles only: blockIdx.x enumerates tile pairs (ti >= tj)
-template <typename T>
+// lower-triangle tiles only: blockIdx.x enumerates tile pairs (ti >= tj).
+// SYRK = true: M = A - P Pᵀ (Q unused); else M = A - (P Qᵀ + Q Pᵀ).
+template <typename T, bool SYRK = false>
 __global__ void __launch_bounds__(NT)
 syr2k_lower_kernel(int m, int k, const T* A, int lda, long long sA, const T* __restrict__ P,
                    int ldp, long long sP, const T* __restrict__ Q, int ldq, long long sQ, T* M,
@@ -370,9 +371,11 @@ syr2k_lower_kernel(int m, int k, const T* A, int lda, long long sA, const T* __r
       const int gi = i0 + i, gj = j0 + i;
       const bool okk = gk < k;
       Pi[kk][i] = (okk && gi < m) ? P[gi + (long long)gk * ldp] : T(0);
-      Qi[kk][i] = (okk && gi < m) ? Q[gi + (long long)gk * ldq] : T(0);
       Pj[kk][i] = (okk && gj < m) ? P[gj + (long long)gk * ldp] : T(0);
-      Qj[kk][i] = (okk && gj < m) ? Q[gj + (long long)gk * ldq] : T(0);
+      if (!SYRK) {
+        Qi[kk][i] = (okk && gi < m) ? Q[gi + (long long)gk * ldq] : T(0);
+        Qj[kk][i] = (okk && gj < m) ? Q[gj + (long long)gk * ldq] : T(0);
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -381,16 +384,22 @@ syr2k_lower_kernel(int m, int k, const T* A, int lda, long long sA, const T* __r
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         pa[s] = Pi[kk][tx + 16 * s];
-        qa[s] = Qi[kk][tx + 16 * s];
         pb[s] = Pj[kk][ty + 16 * s];
-        qb[s] = Qj[kk][ty + 16 * s];
+        if (!SYRK) {
+          qa[s] = Qi[kk][tx + 16 * s];
+          qb[s] = Qj[kk][ty + 16 * s];
+        }
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          acc[p][q] = fma(pa[p], qb[q], acc[p][q]);
-          acc[p][q] = fma(qa[p], pb[q], acc[p][q]);
+          if (SYRK) {
+            acc[p][q] = fma(pa[p], pb[q], acc[p][q]);
+          } else {
+            acc[p][q] = fma(pa[p], qb[q], acc[p][q]);
+            acc[p][q] = fma(qa[p], pb[q], acc[p][q]);
+          }
         }
     }
     __syncthreads();
@@ -439,6 +448,22 @@ void syr2k_lower_batched(int m, int k, const T* A, int lda, long long sA, const 
   dim3 g(nt * (nt + 1) / 2, batch);
   syr2k_lower_kernel<T><<<g, NT, 0, st>>>(m, k, A, lda, sA, P, ldp, sP, Q, ldq, sQ, M, ldm, sM);
 }
+
+template <typename T>
+void syrk_lower_batched(int m, int k, const T* A, int lda, long long sA, const T* P, int ldp,
+                        long long sP, T* M, int ldm, long long sM, int batch, cudaStream_t st) {
+  if (m <= 0 || batch <= 0) return;
+  const int nt = (m + BM - 1) / BM;
+  dim3 g(nt * (nt + 1) / 2, batch);
+  syr2k_lower_kernel<T, true><<<g, NT, 0, st>>>(m, k, A, lda, sA, P, ldp, sP, P, ldp, sP, M, ldm,
+                                                sM);
+}
+
+template void syrk_lower_batched<double>(int, int, const double*, int, long long, const double*,
+                                         int, long long, double*, int, long long, int,
+                                         cudaStream_t);
+template void syrk_lower_batched<float>(int, int, const float*, int, long long, const float*, int,
+                                        long long, float*, int, long long, int, cudaStream_t);
 
 template void gemm_batched<double>(bool, bool, int, int, int, double, const double*, int, long long,
                                    const double*, int, long long, double, double*, int, long long,

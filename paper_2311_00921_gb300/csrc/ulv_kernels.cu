@@ -309,7 +309,7 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
 template <typename T>
 __global__ void __launch_bounds__(NT)
 pchol_kernel(T* Mb, int ldm, long long sM, int b, int c, T* PA, int ldpa, long long sPA,
-             double* logdet_part, int level, int node0, int* status, int panel_only) {
+             double* logdet_part, int level, int node0, int* status) {
   extern __shared__ unsigned char smem_raw[];
   T* P = reinterpret_cast<T*>(smem_raw);   // panel: b rows x NB, column-major ld = b
   __shared__ int fail;
@@ -385,11 +385,10 @@ pchol_kernel(T* Mb, int ldm, long long sM, int b, int c, T* PA, int ldpa, long l
       const int i = e % n1, jj = e / n1;
       if (i >= jj) M[(k0 + i) + (long long)(k0 + jj) * ldm] = P[i + jj * b];
     }
-    // trailing update of the lower triangle, rows/cols >= k0 + kb (left to the
-    // caller in panel_only mode, where c is the panel width)
+    // trailing update of the lower triangle, rows/cols >= k0 + kb
     const int base = kb;   // panel row of the first trailing index
     const int n2 = n1 - kb;
-    if (n2 > 0 && !panel_only) {
+    if (n2 > 0) {
       const int nt = (n2 + 63) / 64;
       const int tx = tid & 15, ty = tid >> 4;
       for (int tp = 0; tp < nt * (nt + 1) / 2; ++tp) {
@@ -448,6 +447,96 @@ pchol_kernel(T* Mb, int ldm, long long sM, int b, int c, T* PA, int ldpa, long l
   }
 }
 
+// a[i] for a run-time i (a static-index select keeps the array in registers)
+template <typename T>
+HSS_DEVINL T reg_select(const T (&a)[NB], int i) {
+  T v = T(0);
+#pragma unroll
+  for (int t = 0; t < NB; ++t)
+    if (t == i) v = a[t];
+  return v;
+}
+
+// ------------------------------------------------------------------ Cholesky panel
+// One panel (kb <= NB columns) of a right-looking blocked Cholesky, one CTA per
+// node; the trailing update is a separate level-wide SYRK.  Warp 0 factors the
+// kb x kb diagonal block in registers (lane i holds row i, the pivot and the
+// column entries travel by shuffles), then every thread solves rows of
+// X L_11ᵀ = M_21 below it in registers against the block kept in shared memory.
+// The node's log-det slot gets (or, with accumulate, adds) 2 Σ log L_jj.
+template <typename T>
+__global__ void __launch_bounds__(NT)
+chol_panel_kernel(T* Mb, int ldm, long long sM, int rows, int kb, double* logdet_part, int level,
+                  int col0, int* status, int accumulate) {
+  __shared__ T Ls[NB][NB + 1];   // Ls[t][j] = L(t, j) of the diagonal block
+  __shared__ T dinv[NB];
+  __shared__ int fail;
+  const int node = blockIdx.x;
+  T* M = Mb + (long long)node * sM;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (wid == 0) {
+    T a[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+      a[t] = (lane < kb && t <= lane) ? M[lane + (long long)t * ldm] : T(0);
+    int bad = -1;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j >= kb) break;
+      const T d = __shfl_sync(0xffffffffu, a[j], j);   // updated A(j, j)
+      if (bad < 0 && !(d > T(0))) bad = j;
+      const T s = sqrt(d);
+      const T inv = T(1) / s;
+      if (lane == j) a[j] = s;
+      if (lane > j) a[j] *= inv;
+      // a[t] -= L(lane, j) L(t, j) for j < t <= lane; L(t, j) is lane t's a[j]
+#pragma unroll
+      for (int t = j + 1; t < NB; ++t) {
+        const T ltj = __shfl_sync(0xffffffffu, a[j], t);
+        if (t <= lane) a[t] = fma(-a[j], ltj, a[t]);
+      }
+    }
+    if (lane == 0) fail = bad >= 0;
+    if (bad >= 0) {
+      if (lane == 0) report_failure(status, -3 /*NOT_SPD*/, level, node, col0 + bad);
+    } else {
+#pragma unroll
+      for (int t = 0; t < NB; ++t)
+        if (lane < kb && t <= lane) {
+          M[lane + (long long)t * ldm] = a[t];
+          Ls[lane][t] = a[t];
+        }
+      const T dg = reg_select(a, lane);
+      if (lane < kb) dinv[lane] = T(1) / dg;
+      double ld = lane < kb ? log((double)dg) : 0.0;
+      ld = warp_sum(ld);
+      if (lane == 0 && logdet_part) {
+        if (accumulate)
+          logdet_part[node] += 2.0 * ld;
+        else
+          logdet_part[node] = 2.0 * ld;
+      }
+    }
+  }
+  __syncthreads();
+  if (fail) return;
+  for (int i = kb + tid; i < rows; i += NT) {
+    T x[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) x[t] = t < kb ? M[i + (long long)t * ldm] : T(0);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j >= kb) break;
+      x[j] *= dinv[j];
+#pragma unroll
+      for (int t = j + 1; t < NB; ++t) x[t] = fma(-x[j], Ls[t][j], x[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+      if (t < kb) M[i + (long long)t * ldm] = x[t];
+  }
+}
+
 // ------------------------------------------------------------------ triangular sweeps
 // forward: y (b x nrhs, smem) := [L^RR⁻¹ y^R ; y^S - L^SR L^RR⁻¹ y^R]
 template <typename T>
@@ -467,18 +556,26 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
   __syncthreads();
   for (int k0 = 0; k0 < c; k0 += NB) {
     const int kb = min(NB, c - k0);
-    // diagonal block: warp w handles right-hand sides w, w + nw, ...
-    for (int j = wid; j < nrhs; j += nw) {
-      T* yj = y + j * b + k0;
-      T v = lane < kb ? yj[lane] : T(0);
-      const T lii = lane < kb ? M[(k0 + lane) + (long long)(k0 + lane) * ldm] : T(1);
-      for (int t = 0; t < kb; ++t) {
-        T zt = __shfl_sync(0xffffffffu, v, t);
-        zt = zt / __shfl_sync(0xffffffffu, lii, t);
-        if (lane == t) v = zt;
-        if (lane > t && lane < kb) v -= M[(k0 + lane) + (long long)(k0 + t) * ldm] * zt;
+    // diagonal block: warp w handles right-hand sides w, w + nw, ...; lane i
+    // keeps row i of the block in registers (loaded once, outside the chain)
+    {
+      T lrow[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t)
+        lrow[t] = (lane < kb && t <= lane) ? M[(k0 + lane) + (long long)(k0 + t) * ldm] : T(0);
+      const T inv = lane < kb ? T(1) / reg_select(lrow, lane) : T(0);
+      for (int j = wid; j < nrhs; j += nw) {
+        T* yj = y + j * b + k0;
+        T v = lane < kb ? yj[lane] : T(0);
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          if (t >= kb) break;
+          if (lane == t) v *= inv;
+          const T zt = __shfl_sync(0xffffffffu, v, t);
+          if (lane > t) v = fma(-lrow[t], zt, v);
+        }
+        if (lane < kb) yj[lane] = v;
       }
-      if (lane < kb) yj[lane] = v;
     }
     __syncthreads();
     // update every row below the block (the S rows included: L^SR lives there)
@@ -560,18 +657,27 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       }
     }
     __syncthreads();
-    // diagonal block, transposed back substitution
-    for (int j = wid; j < nrhs; j += nw) {
-      T* yj = y + j * b + k0;
-      T v = lane < kb ? yj[lane] : T(0);
-      for (int t = kb - 1; t >= 0; --t) {
-        T xt = __shfl_sync(0xffffffffu, v, t);
-        const T ltt = M[(k0 + t) + (long long)(k0 + t) * ldm];
-        xt = xt / ltt;
-        if (lane == t) v = xt;
-        if (lane < t) v -= M[(k0 + t) + (long long)(k0 + lane) * ldm] * xt;
+    // diagonal block, transposed back substitution; lane i keeps column i of
+    // the block (L(t, i), t >= i) in registers
+    {
+      T lcol[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t)
+        lcol[t] = (lane < kb && t >= lane && t < kb) ? M[(k0 + t) + (long long)(k0 + lane) * ldm]
+                                                      : T(0);
+      const T inv = lane < kb ? T(1) / reg_select(lcol, lane) : T(0);
+      for (int j = wid; j < nrhs; j += nw) {
+        T* yj = y + j * b + k0;
+        T v = lane < kb ? yj[lane] : T(0);
+#pragma unroll
+        for (int tt = NB - 1; tt >= 0; --tt) {
+          if (tt >= kb) continue;
+          if (lane == tt) v *= inv;
+          const T xt = __shfl_sync(0xffffffffu, v, tt);
+          if (lane < tt) v = fma(-lcol[tt], xt, v);
+        }
+        if (lane < kb) yj[lane] = v;
       }
-      if (lane < kb) yj[lane] = v;
     }
     __syncthreads();
   }
@@ -646,18 +752,42 @@ cudaError_t launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int l
   const size_t sm = pchol_smem<T>(b);
   if (!smem_opt_in(pchol_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
   pchol_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, PA, ldpa, sPA, logdet_part, level,
-                                         node0, status, 0);
+                                         node0, status);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_chol_panel(T* M, int ldm, int rows, int kb, double* logdet_slot, int level,
-                              int col0, int* status, cudaStream_t st) {
-  const size_t sm = pchol_smem<T>(rows);
-  if (!smem_opt_in(pchol_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
-  (void)col0;   // failures report the column within the panel
-  pchol_kernel<T><<<1, NT, sm, st>>>(M, ldm, 0, rows, kb, nullptr, 0, 0, logdet_slot, level, 0,
-                                     status, 1);
+cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, double* logdet_part,
+                              int level, int col0, int* status, int nodes, bool accumulate,
+                              cudaStream_t st) {
+  if (kb < 1 || kb > NB || rows < kb) return cudaErrorInvalidValue;
+  chol_panel_kernel<T><<<nodes, NT, 0, st>>>(M, ldm, sM, rows, kb, logdet_part, level, col0,
+                                             status, accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Â^SS of every node (lower triangle at M[c:, c:]) into its parent's diagonal
+// block at (off, off), both triangles (the merge of Alg. 2 line 4)
+template <typename T>
+__global__ void scatter_ss_kernel(const T* __restrict__ Mb, int ldm, long long sM, int c, int r,
+                                  T* PA, int ldpa, long long sPA) {
+  const int node = blockIdx.x;
+  const T* M = Mb + (long long)node * sM;
+  T* A = PA + (long long)(node >> 1) * sPA;
+  const int off = (node & 1) * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    if (i < j) continue;
+    const T v = M[(c + i) + (long long)(c + j) * ldm];
+    A[(off + i) + (long long)(off + j) * ldpa] = v;
+    A[(off + j) + (long long)(off + i) * ldpa] = v;
+  }
+}
+
+template <typename T>
+cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T* PA, int ldpa,
+                              long long sPA, int nodes, cudaStream_t st) {
+  scatter_ss_kernel<T><<<nodes, NT, 0, st>>>(M, ldm, sM, c, r, PA, ldpa, sPA);
   return cudaGetLastError();
 }
 
@@ -695,7 +825,9 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
   template cudaError_t launch_trsv_bwd<T>(const T*, int, long long, int, int, T*, int, long long, \
                                           int, const T*, int, long long, int, cudaStream_t);      \
   template size_t ql_smem<T>(int, int);                                                          \
-  template cudaError_t launch_chol_panel<T>(T*, int, int, int, double*, int, int, int*,           \
-                                            cudaStream_t);
+  template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int,     \
+                                            int*, int, bool, cudaStream_t);                       \
+  template cudaError_t launch_scatter_ss<T>(const T*, int, long long, int, int, T*, int,           \
+                                            long long, int, cudaStream_t);
 INST(double)
 INST(float)

@@ -29,9 +29,17 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
 template <typename T>
 size_t ql_smem(int b, int r);
 
-// One panel of a blocked Cholesky: factor the kb x kb diagonal block at the
-// top of the rows x rows matrix M (ld ldm) and solve the rows below it; the
-// trailing update is left to the caller.  Writes 2 Σ log diag to *logdet_slot.
+// One panel of a blocked Cholesky, for every node of a batch (stride sM): factor
+// the kb x kb diagonal block at the top of each rows x rows matrix M (ld ldm)
+// and solve the rows below it; the trailing update is left to the caller.
+// Writes (or, with accumulate, adds) 2 Σ log diag to logdet_part[node].
 template <typename T>
-cudaError_t launch_chol_panel(T* M, int ldm, int rows, int kb, double* logdet_slot, int level,
-                              int col0, int* status, cudaStream_t st);
+cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, double* logdet_part,
+                              int level, int col0, int* status, int nodes, bool accumulate,
+                              cudaStream_t st);
+
+// The merge of Alg. 2 line 4 as its own pass: Â^SS of node i (lower triangle
+// of M[c:, c:], r x r) into block (i & 1) of parent i / 2's diagonal, both triangles.
+template <typename T>
+cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T* PA, int ldpa,
+                              long long sPA, int nodes, cudaStream_t st);
