@@ -174,7 +174,10 @@ KERNEL_SOURCES = {"tc_gemm": "tc_gemm_kernel", "tc_syr2k": "tc_gemm_kernel",
                   "gemm": "gemm_tile_kernel", "syr2k": "syr2k_lower_kernel",
                   "pchol": "pchol_kernel", "ql": "ql_basis_kernel",
                   "gemm_skinny": "gemm_n16_kernel", "trsv_fwd": "trsv_fwd_kernel",
-                  "trsv_bwd": "trsv_bwd_kernel", "other": "logdet_reduce_kernel"}
+                  "trsv_bwd": "trsv_bwd_kernel", "other": "logdet_reduce_kernel",
+                  "pair_gemm": "df_gemm_kernel"}
+# pair-of-FP32 arithmetic: 15 FP32 instructions per multiply-add (2 flops)
+PAIR_OPS_PER_FLOP = 7.5
 
 
 def workload(args):
@@ -272,7 +275,10 @@ def measured_peaks(torch):
     return peaks
 
 
-PEAK_SOURCE = {"f64": "cuBLAS DGEMM 8192^3 (FP64 pipe) measured in this run",
+PEAK_SOURCE = {"pair32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured in this run, "
+                         "/ 7.5: the pair arithmetic spends 15 FP32 instructions per "
+                         "multiply-add",
+               "f64": "cuBLAS DGEMM 8192^3 (FP64 pipe) measured in this run",
                "f32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured in this run",
                "tf32": "cuBLAS TF32 GEMM 8192^3 measured in this run (x3 split: 3 MMAs per "
                        "algorithmic product, so frac <= 1/3)",
@@ -280,10 +286,10 @@ PEAK_SOURCE = {"f64": "cuBLAS DGEMM 8192^3 (FP64 pipe) measured in this run",
                        "algorithmic product, so frac <= 1/3)"}
 
 
-def timed_steps(torch, dev, b, x, prec, steps, clocks=None):
+def timed_steps(torch, dev, b, x, prec, steps, clocks=None, residual="fp64"):
     """K timed factor+solve steps on the current stream; returns a dict."""
     def step():
-        dev.factorize(prec)
+        dev.factorize(prec, residual=residual)
         dev.solve(b, x)
     torch.cuda.synchronize()
     if clocks:
@@ -304,7 +310,7 @@ def timed_steps(torch, dev, b, x, prec, steps, clocks=None):
     # factor / solve split (one untimed pass)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record()
-    dev.factorize(prec)
+    dev.factorize(prec, residual=residual)
     e[1].record()
     dev.solve(b, x)
     e[2].record()
@@ -322,11 +328,14 @@ def roofline_of(tr, peaks, steps, prec_mode="fp64"):
     achieved = dfl / (dms / 1e3) / 1e12 if dms > 0 else 0.0
     kname = KERNEL_SOURCES[kind]
     peak = peaks.get(prec) if peaks else None
+    if kind == "pair_gemm":
+        prec = "pair32"
+        peak = peaks["f32"] / PAIR_OPS_PER_FLOP if peaks else None
     total = sum(v[0] for v in tr.values())
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if peak else None,
             "traffic": traffic_record(kname) if prec == "f64" else None,
-            "kernel": f"{kname} ({ {'f64': 'FP64', 'f32': 'FP32', 'tf32': 'TF32 x3', 'bf16': 'BF16 x3'}.get(prec, prec)})",
+            "kernel": f"{kname} ({ {'f64': 'FP64', 'f32': 'FP32', 'tf32': 'TF32 x3', 'bf16': 'BF16 x3', 'pair32': 'pair-of-FP32'}.get(prec, prec)})",
             "peak_source": PEAK_SOURCE.get(prec),
             "kernel_ms_per_launch": dms / max(1, dn), "kernel_share": dms / total,
             "per_kernel_ms_per_step": {k: v[0] / steps for k, v in sorted(tr.items())},
@@ -359,13 +368,14 @@ def run_ours(args):
     fl_step = factor_flops(w.levels, w.leaf, w.rank) + solve_flops(w.levels, w.leaf, w.rank,
                                                                     w.nrhs)
 
+    resid = args.residual if prec != "fp64" else "fp64"
     for _ in range(args.warmup):
-        dev.factorize(prec)
+        dev.factorize(prec, residual=resid)
         dev.solve(b, x)
     peaks = measured_peaks(torch) if rank == 0 else None
     if dist:
         dist.barrier()
-    head = timed_steps(torch, dev, b, x, prec, args.steps, ClockSampler(local))
+    head = timed_steps(torch, dev, b, x, prec, args.steps, ClockSampler(local), resid)
     ms = head["ms"]
     if dist:
         tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -378,6 +388,20 @@ def run_ours(args):
     rel = (torch.linalg.vector_norm(r, dim=0) / torch.linalg.vector_norm(b, dim=0)).max().item()
     logdet = dev.logdet()
     x_head = x.clone()
+
+    # the same mixed path with the refinement residual in FP64 (for comparison)
+    mixed_r64 = None
+    if resid != "fp64" and not args.no_fp64_compare:
+        for _ in range(2):
+            dev.factorize(prec, residual="fp64")
+            dev.solve(b, x)
+        g = timed_steps(torch, dev, b, x, prec, args.steps, residual="fp64")
+        rr = b - dev.matvec(x)
+        mixed_r64 = {"ms_per_step": g["ms"] / args.steps, "factor_ms": g["factor_ms"],
+                     "solve_ms": g["solve_ms"],
+                     "max_rel_residual": (torch.linalg.vector_norm(rr, dim=0)
+                                          / torch.linalg.vector_norm(b, dim=0)).max().item(),
+                     "ir_iterations": g["info"]["ir_iters"]}
 
     fp64 = None
     if prec != "fp64" and not args.no_fp64_compare:
@@ -421,7 +445,10 @@ def run_ours(args):
                "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "rank": w.rank,
                           "levels": w.levels, "nrhs": w.nrhs,
                           "precision": prec if prec == "fp64" else
-                          f"{prec} factor + FP64 iterative refinement to 1e-12",
+                          f"{prec} factor + iterative refinement to 1e-12 (FP64 iterate "
+                          f"and test; residual in "
+                          f"{'pair-of-FP32, 48-bit' if resid == 'pair32' else 'FP64'})",
+                          "residual": resid,
                           "parallelism": f"replicas{world}" if world > 1 else "single",
                           "l2": "HSS data (1.54 GB) and factors exceed L2; no flush",
                           "flop_model": "canonical dense-QtDQ model per node (4b^3 + form-Q "
@@ -430,7 +457,7 @@ def run_ours(args):
                "factor_ms": head["factor_ms"], "solve_ms": head["solve_ms"],
                "check": {"max_rel_residual": rel, "logdet": logdet,
                          "ir_iterations": info["ir_iters"], "ir_resid": info["ir_resid"]},
-               "fp64": fp64,
+               "fp64": fp64, "mixed_fp64_residual": mixed_r64,
                "roofline": roofline_of(head["trace"], peaks, args.steps, prec),
                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
                "gpu_launches": head["launches"]}
@@ -539,7 +566,8 @@ def run_e2e(args, h, w, b_host, prec, fl_step, world, dist):
         hss._check(lib.hss_create(ctypes.byref(shape), D.data_ptr(), U.data_ptr(), E.data_ptr(),
                                   S.data_ptr(), 0, ctypes.byref(out)), "hss_create")
         st = torch.cuda.current_stream()
-        opt = hss.Options(hss.PRECISIONS[prec], 30, 1e-12)
+        opt = hss.Options(hss.PRECISIONS[prec], 30, 1e-12,
+                          hss.RESIDUALS[args.residual if prec != "fp64" else "fp64"], 0)
         hss._check(lib.hss_factorize(out, ctypes.byref(opt), st.cuda_stream), "hss_factorize")
         bd.copy_(bh, non_blocking=True)
         hss._check(lib.hss_solve(out, bd.data_ptr(), xd.data_ptr(), w.nrhs, w.n, st.cuda_stream),
@@ -567,6 +595,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "tf32", "bf16", "fp32"],
                     help="factor arithmetic; non-fp64 modes refine in FP64 to 1e-12")
+    ap.add_argument("--residual", default="pair32", choices=["fp64", "pair32"],
+                    help="arithmetic of the refinement residual of the mixed modes")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched uneven workload with this many matrices instead")

@@ -80,10 +80,22 @@ typedef struct {
   int32_t levels; /* L >= 1 */
 } hss_shape;
 
+/* Arithmetic of the refinement residual r = b - A x of the mixed modes.
+ * HSS_RESIDUAL_FP64: the HSS matvec in FP64 (the chip's FP64 pipe).
+ * HSS_RESIDUAL_PAIR32: the same matvec with every value held as an unevaluated
+ * sum of two FP32 numbers (48-bit significand) and every product and sum done
+ * with error-free FP32 transformations on the FP32 pipe; a dot product of
+ * length K then carries a relative error of about sqrt(K) 2^-48 (~1e-13 for the
+ * leaf products), two orders below the 1e-12 that the refinement stops at.
+ * The update x += d and the convergence test stay FP64. */
+typedef enum { HSS_RESIDUAL_FP64 = 0, HSS_RESIDUAL_PAIR32 = 1 } hss_residual;
+
 typedef struct {
   int32_t precision; /* hss_precision */
   int32_t ir_max_it; /* refinement iteration limit (mixed modes), e.g. 30 */
   double ir_tol;     /* stop when every column has ‖b - A x‖₂ / ‖b‖₂ <= ir_tol */
+  int32_t residual;  /* hss_residual (mixed modes) */
+  int32_t reserved;  /* 0 */
 } hss_options;
 
 /* Create a device-resident HSS object from its generators (format above).
@@ -129,6 +141,16 @@ int hss_logdet(hss_t h, double* out);
  * pass, leaf blocks.  FP64.  x and y are device pointers (n x nrhs, ld), must
  * not overlap.  Asynchronous.  Needs no factorization. */
 int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, void* stream);
+
+/* y = A x as hss_matvec, every product and sum in pair-of-FP32 arithmetic
+ * (HSS_RESIDUAL_PAIR32): the generators are split once into hi = fl32(g) and
+ * lo = fl32(g - hi) (done by any mixed factorization, or by the first call),
+ * x is split per column after scaling by a power of two near 1 / ‖x_j‖₂, and y
+ * is returned in FP64, scaled back.  Relative error about sqrt(K) 2^-48 of
+ * |A| |x| for inner dimension K.  Allocates the FP32 workspace on first use.
+ * x and y are device pointers (n x nrhs, ld), must not overlap.  Asynchronous.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, void* stream);
 
 /* y = A x like hss_matvec, but allocating nothing: no cudaMalloc, no cudaFree,
  * no allocating library call.  The paper has no counterpart; this entry point
@@ -191,8 +213,9 @@ typedef enum {
   HSS_K_OTHER = 7,     /* log-det reduction, precision conversion, refinement helpers */
   HSS_K_TC_GEMM = 8,   /* tensor-core (tcgen05) W = A V of the mixed diagonal product */
   HSS_K_TC_SYR2K = 9,  /* tensor-core (tcgen05) rank-2r update of the mixed diagonal product */
-  HSS_K_COUNT = 10,
-  HSS_K_FP32 = 10      /* added to a class: the same kernel run in FP32 (mixed modes) */
+  HSS_K_PAIR_GEMM = 10, /* pair-of-FP32 GEMM of the refinement residual (logged as FP32) */
+  HSS_K_COUNT = 11,
+  HSS_K_FP32 = 11      /* added to a class: the same kernel run in FP32 (mixed modes) */
 } hss_kernel_kind;
 
 /* Per-kernel timing: with enable = 1 every later launch of the object is

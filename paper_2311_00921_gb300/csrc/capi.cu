@@ -16,6 +16,7 @@
 
 #include "../../include/hss.h"
 #include "common.cuh"
+#include "dfgemm.cuh"
 #include "ir_kernels.cuh"
 #include "tc_gemm.cuh"
 #include "ulv_kernels.cuh"
@@ -70,7 +71,7 @@ struct hss_s {
   int a0inv_valid = 0;
   double* rbuf = nullptr;              // n x kSolveCols residual
   double* bbuf = nullptr;              // n x kSolveCols copy of b (x aliasing b)
-  double* norms = nullptr;             // 4 x kSolveCols: |b|, 1/|b|, |r|, 1/|r|
+  double* norms = nullptr;             // 6 x kSolveCols: |b|, 1/|b|, |r|, 1/|r|, |x|, 1/|x|
   double* logdet_part = nullptr;       // 2^(L+1) - 1 node contributions
   double* logdet_val = nullptr;
   int* status = nullptr;
@@ -82,6 +83,13 @@ struct hss_s {
   TcMode tc_mode = TcMode::TF32x3;
   int ir_max_it = 30;
   double ir_tol = 1e-12;
+  int residual = HSS_RESIDUAL_FP64;    // arithmetic of the refinement residual
+  // pair-of-FP32 generators (hi parts are the FP32 factor's converted copies)
+  // and the pair matvec's vectors, in the FP32 arena
+  float *Dl = nullptr, *Ul = nullptr, *El = nullptr, *Sl = nullptr;
+  float *xs_h = nullptr, *xs_l = nullptr, *yt_h = nullptr, *yt_l = nullptr;
+  std::vector<float*> xp_h, xp_l, yp_h, yp_l;
+  int pairs_valid = 0;
   cudaStream_t last_stream = nullptr;
   // basis-completion chain runs ahead on its own stream; one event per level
   cudaStream_t qstream = nullptr;
@@ -186,7 +194,7 @@ size_t layout_main(hss_s* h, char* base) {
   h->root_vec2 = bp.take<double>((size_t)2 * r * kSolveCols);
   h->rbuf = bp.take<double>((size_t)h->n * kSolveCols);
   h->bbuf = bp.take<double>((size_t)h->n * kSolveCols);
-  h->norms = bp.take<double>(4 * kSolveCols);
+  h->norms = bp.take<double>(6 * kSolveCols);
   h->logdet_part = bp.take<double>((size_t)(2 * nL - 1) + kRootPanels);
   h->logdet_val = bp.take<double>(1);
   h->status = bp.take<int>(8);
@@ -206,6 +214,18 @@ size_t layout_f32(hss_s* h, char* base) {
   layout_factor<float>(bp, f, L, leaf, r);
   f.d = bp.take<float>((size_t)h->n * kSolveCols);
   h->zq32 = bp.take<float>((size_t)nL * r * r);
+  h->Dl = bp.take<float>(nL * leaf * leaf);
+  h->Ul = bp.take<float>(nL * leaf * r);
+  h->El = bp.take<float>(std::max<long long>(h->esz, 1));
+  h->Sl = bp.take<float>(h->ssz);
+  h->xs_h = bp.take<float>((size_t)h->n * kSolveCols);
+  h->xs_l = bp.take<float>((size_t)h->n * kSolveCols);
+  h->yt_h = bp.take<float>((size_t)h->n * kSolveCols);
+  h->yt_l = bp.take<float>((size_t)h->n * kSolveCols);
+  for (auto* v : {&h->xp_h, &h->xp_l, &h->yp_h, &h->yp_l}) {
+    v->assign(L + 1, nullptr);
+    for (int l = 1; l <= L; ++l) (*v)[l] = bp.take<float>((size_t(1) << l) * r * kSolveCols);
+  }
   f.D = f.Dc;
   f.U = f.Uc;
   f.E = f.Ec;
@@ -443,6 +463,8 @@ int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
   return check_launch();
 }
 
+cudaError_t split_generators(hss_s* h, cudaStream_t st);
+
 int factorize(hss_s* h, int prec, cudaStream_t st) {
   const int L = h->L, r = h->rank;
   cudaMemsetAsync(h->status, 0, 8 * sizeof(int), st);
@@ -453,22 +475,9 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
     root = h->f64.lv[0].A;
   } else {
     Factor<float>& f = h->f32;
-    {   // the generators in FP32 (part of every factorization)
-      Launch k(h, HSS_K_OTHER, 0.0, st);
-      launch_f64_to_f32(h->D, f.Dc, (1LL << L) * h->leaf * h->leaf, st);
-    }
-    {
-      Launch k(h, HSS_K_OTHER, 0.0, st);
-      launch_f64_to_f32(h->U, f.Uc, (1LL << L) * h->leaf * r, st);
-    }
-    if (h->esz) {
-      Launch k(h, HSS_K_OTHER, 0.0, st);
-      launch_f64_to_f32(h->E, f.Ec, h->esz, st);
-    }
-    {
-      Launch k(h, HSS_K_OTHER, 0.0, st);
-      launch_f64_to_f32(h->S, f.Sc, h->ssz, st);
-    }
+    // the generators in FP32 (part of every factorization), with their
+    // low-order FP32 parts for the pair-arithmetic residual
+    HSS_TRY(split_generators(h, st));
     int rc = factor_levels<float>(h, f, h->zq32, st);
     if (rc) return rc;
     {   // the root block goes to FP64 for the root Cholesky
@@ -610,6 +619,108 @@ int matvec_fp64(hss_s* h, const double* x, int ldx, double* y, int ldy, int nrhs
   return HSS_OK;
 }
 
+// hi = fl32(g) into the FP32 factor's generator copies, lo = fl32(g - hi)
+cudaError_t split_generators(hss_s* h, cudaStream_t st) {
+  const int L = h->L, r = h->rank;
+  Factor<float>& f = h->f32;
+  const long long nL = 1LL << L;
+  cudaError_t e = cudaSuccess;
+  {
+    Launch k(h, HSS_K_OTHER, 0.0, st);
+    e = launch_df_split(h->D, f.Dc, h->Dl, nL * h->leaf * h->leaf, st);
+  }
+  if (e == cudaSuccess) {
+    Launch k(h, HSS_K_OTHER, 0.0, st);
+    e = launch_df_split(h->U, f.Uc, h->Ul, nL * h->leaf * r, st);
+  }
+  if (e == cudaSuccess && h->esz) {
+    Launch k(h, HSS_K_OTHER, 0.0, st);
+    e = launch_df_split(h->E, f.Ec, h->El, h->esz, st);
+  }
+  if (e == cudaSuccess) {
+    Launch k(h, HSS_K_OTHER, 0.0, st);
+    e = launch_df_split(h->S, f.Sc, h->Sl, h->ssz, st);
+  }
+  if (e == cudaSuccess) h->pairs_valid = 1;
+  return e;
+}
+
+// The FP32 arena (converted generators, FP32 factor, pair matvec buffers),
+// allocated on first use.
+int ensure_f32_arena(hss_s* h) {
+  if (h->f32.arena) return HSS_OK;
+  const size_t bytes = layout_f32(h, nullptr);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HSS_ERR_OOM;
+  }
+  h->f32.arena = mem;
+  h->f32.bytes = bytes;
+  layout_f32(h, static_cast<char*>(mem));
+  return HSS_OK;
+}
+
+#define DF_TRY(call)                                  \
+  do {                                                \
+    if ((call) != cudaSuccess) return HSS_ERR_CUDA;   \
+  } while (0)
+
+// y = A x (nc <= kSolveCols columns) with the same up-sweep / coupling /
+// down-sweep / leaf structure as matvec_fp64, every product in pair-of-FP32
+// arithmetic (dfgemm.cu).  x enters scaled per column by a power of two near
+// 1 / |x_j| so that its pairs stay in range; y leaves scaled back, in FP64.
+int matvec_pair(hss_s* h, const double* x, int ldx, double* y, int ldy, int nc, cudaStream_t st) {
+  const int L = h->L, r = h->rank, leaf = h->leaf, n = h->n;
+  const long long rr = (long long)r * r;
+  const int nL = 1 << L;
+  const Factor<float>& f = h->f32;
+  double* xn = h->norms + 4 * kSolveCols;
+  {
+    Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
+    launch_col_norms(x, ldx, n, nc, xn, xn + kSolveCols, st);
+  }
+  {
+    Launch k(h, HSS_K_OTHER, 0.0, st);
+    DF_TRY(launch_df_split_cols(x, ldx, n, nc, xn, h->xs_h, h->xs_l, n, st));
+  }
+  auto df = [&](bool ta, int m, int k, const float* Ah, const float* Al, int lda, long long sA,
+                const float* Bh, const float* Bl, int ldb, long long sB, bool acc, float* Ch,
+                float* Cl, double* C64, int ldc64, int ldc, long long sC, int batch) {
+    Launch kk(h, HSS_K_PAIR_GEMM, 2.0 * m * nc * (double)k * batch, st, true);
+    return df_gemm(ta, m, nc, k, Ah, Al, lda, sA, Bh, Bl, ldb, sB, acc, Ch, Cl, C64, ldc64, xn,
+                   ldc, sC, batch, st);
+  };
+  // up-sweep: x̂_L = Uᵀ x, x̂_l = E_lᵀ [x̂_{l+1}(2p); x̂_{l+1}(2p+1)]
+  DF_TRY(df(true, r, leaf, f.Uc, h->Ul, leaf, (long long)leaf * r, h->xs_h, h->xs_l, n, leaf,
+            false, h->xp_h[L], h->xp_l[L], nullptr, 0, nL * r, r, nL));
+  for (int l = L - 1; l >= 1; --l)
+    DF_TRY(df(true, r, 2 * r, f.Ec + h->Eoff[l], h->El + h->Eoff[l], 2 * r, 2 * rr, h->xp_h[l + 1],
+              h->xp_l[l + 1], (2 << l) * r, 2 * r, false, h->xp_h[l], h->xp_l[l], nullptr, 0,
+              (1 << l) * r, r, 1 << l));
+  // sibling couplings of every level (these initialise ŷ)
+  for (int l = 1; l <= L; ++l) {
+    const float* Sh = f.Sc + h->Soff[l];
+    const float* Sl = h->Sl + h->Soff[l];
+    const int ldl = (1 << l) * r;
+    DF_TRY(df(false, r, r, Sh, Sl, r, rr, h->xp_h[l], h->xp_l[l], ldl, 2 * r, false,
+              h->yp_h[l] + r, h->yp_l[l] + r, nullptr, 0, ldl, 2 * r, 1 << (l - 1)));
+    DF_TRY(df(true, r, r, Sh, Sl, r, rr, h->xp_h[l] + r, h->xp_l[l] + r, ldl, 2 * r, false,
+              h->yp_h[l], h->yp_l[l], nullptr, 0, ldl, 2 * r, 1 << (l - 1)));
+  }
+  // down-sweep: ŷ_{l+1}(children) += E_l ŷ_l
+  for (int l = 1; l <= L - 1; ++l)
+    DF_TRY(df(false, 2 * r, r, f.Ec + h->Eoff[l], h->El + h->Eoff[l], 2 * r, 2 * rr, h->yp_h[l],
+              h->yp_l[l], (1 << l) * r, r, true, h->yp_h[l + 1], h->yp_l[l + 1], nullptr, 0,
+              (2 << l) * r, 2 * r, 1 << l));
+  // leaves: y = D x + U ŷ, the second product writing FP64
+  DF_TRY(df(false, leaf, leaf, f.Dc, h->Dl, leaf, (long long)leaf * leaf, h->xs_h, h->xs_l, n,
+            leaf, false, h->yt_h, h->yt_l, nullptr, 0, n, leaf, nL));
+  DF_TRY(df(false, leaf, r, f.Uc, h->Ul, leaf, (long long)leaf * r, h->yp_h[L], h->yp_l[L], nL * r,
+            r, true, h->yt_h, h->yt_l, y, ldy, n, leaf, nL));
+  return check_launch();
+}
+
 int read_status(hss_s* h, int* st_host) {
   cudaError_t e = cudaMemcpy(st_host, h->status, 8 * sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return HSS_ERR_CUDA;
@@ -661,7 +772,9 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
     int it = 0;
     double rel = 0.0;
     for (;; ++it) {
-      rc = matvec_fp64(h, xc, ld, h->rbuf, n, nc, st);   // rbuf: n x nc, ld = n
+      rc = h->residual == HSS_RESIDUAL_PAIR32
+               ? matvec_pair(h, xc, ld, h->rbuf, n, nc, st)    // rbuf: n x nc, ld = n
+               : matvec_fp64(h, xc, ld, h->rbuf, n, nc, st);
       if (rc) return rc;
       {
         Launch k(h, HSS_K_OTHER, (double)n * nc, st);
@@ -795,22 +908,18 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
       prec != HSS_MIXED_BF16)
     return HSS_ERR_INVALID_ARG;
   if (opt && (opt->ir_max_it < 0 || !(opt->ir_tol >= 0.0))) return HSS_ERR_INVALID_ARG;
+  if (opt && opt->residual != HSS_RESIDUAL_FP64 && opt->residual != HSS_RESIDUAL_PAIR32)
+    return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
-  if (prec != HSS_FP64 && !h->f32.arena) {
-    const size_t bytes = layout_f32(h, nullptr);
-    void* mem = nullptr;
-    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return HSS_ERR_OOM;
-    }
-    h->f32.arena = mem;
-    h->f32.bytes = bytes;
-    layout_f32(h, static_cast<char*>(mem));
+  if (prec != HSS_FP64) {
+    const int rc = ensure_f32_arena(h);
+    if (rc) return rc;
   }
   if (opt) {
     h->ir_max_it = opt->ir_max_it;
     h->ir_tol = opt->ir_tol;
+    h->residual = opt->residual;
   }
   h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
   h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;
@@ -848,6 +957,23 @@ int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, vo
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->last_stream = st;
   return matvec_fp64(h, x, ld, y, ld, nrhs, st);
+}
+
+int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld,
+                    void* stream) {
+  if (!h || !x || !y || nrhs < 0 || ld < h->n || x == y) return HSS_ERR_INVALID_ARG;
+  if (nrhs == 0) return HSS_OK;
+  int rc = ensure_f32_arena(h);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->last_stream = st;
+  if (!h->pairs_valid && split_generators(h, st) != cudaSuccess) return HSS_ERR_CUDA;
+  for (int j0 = 0; j0 < nrhs; j0 += kSolveCols) {
+    const int nc = std::min(kSolveCols, nrhs - j0);
+    rc = matvec_pair(h, x + (long long)j0 * ld, ld, y + (long long)j0 * ld, ld, nc, st);
+    if (rc) return rc;
+  }
+  return HSS_OK;
 }
 
 int hss_sync(hss_t h) {

@@ -32,7 +32,11 @@ class Shape(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("ir_max_it", ctypes.c_int32),
-                ("ir_tol", ctypes.c_double)]
+                ("ir_tol", ctypes.c_double), ("residual", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+RESIDUALS = {"fp64": 0, "pair32": 1}
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -42,6 +46,7 @@ SIGNATURES = {
     "hss_solve": (_c_int, [_p, _p, _p, ctypes.c_int32, ctypes.c_int32, _p]),
     "hss_logdet": (_c_int, [_p, ctypes.POINTER(_c_double)]),
     "hss_matvec": (_c_int, [_p, _p, _p, ctypes.c_int32, ctypes.c_int32, _p]),
+    "hss_matvec_pair": (_c_int, [_p, _p, _p, ctypes.c_int32, ctypes.c_int32, _p]),
     "hss_sync": (_c_int, [_p]),
     "hss_last_info": (_c_int, [_p, _i32p, _i32p, _i32p, _i32p, ctypes.POINTER(_c_double)]),
     "hss_export": (_c_int, [_p, ctypes.c_int32, ctypes.c_int32, _p, ctypes.c_size_t]),
@@ -161,8 +166,11 @@ class HSS:
         except Exception:
             pass
 
-    def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, stream=None):
-        opt = Options(PRECISIONS[precision], ir_max_it, ir_tol)
+    def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, residual="fp64",
+                  stream=None):
+        """residual: arithmetic of the refinement residual of the mixed modes,
+        "fp64" or "pair32" (pairs of FP32 numbers, 48-bit significands)."""
+        opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual], 0)
         _check(load().hss_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_factorize")
         self.precision = precision
@@ -192,6 +200,20 @@ class HSS:
         _check(load().hss_matvec(self._h, xp, yp, nrhs, ld, _stream_ptr(stream)), "hss_matvec")
         return y
 
+    def matvec_pair(self, x, y=None, stream=None):
+        """y = A x in pair-of-FP32 arithmetic (hss_matvec_pair)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x) if x.dim() == 1 else torch.empty(
+                (x.shape[1], x.shape[0]), dtype=x.dtype, device=x.device).t()
+        xp, nrhs, ld = _mat_args(x)
+        yp, nrhs2, ld2 = _mat_args(y)
+        if nrhs != nrhs2 or ld != ld2:
+            raise ValueError("x and y need the same shape and leading dimension")
+        _check(load().hss_matvec_pair(self._h, xp, yp, nrhs, ld, _stream_ptr(stream)),
+               "hss_matvec_pair")
+        return y
+
     def logdet(self) -> float:
         out = ctypes.c_double()
         _check(load().hss_logdet(self._h, ctypes.byref(out)), "hss_logdet")
@@ -209,7 +231,7 @@ class HSS:
                 "ir_iters": it.value, "ir_resid": res.value}
 
     KERNELS = ("ql", "gemm", "gemm_skinny", "syr2k", "pchol", "trsv_fwd", "trsv_bwd", "other",
-               "tc_gemm", "tc_syr2k")
+               "tc_gemm", "tc_syr2k", "pair_gemm")
 
     def trace(self, enable: bool):
         _check(load().hss_trace(self._h, 1 if enable else 0), "hss_trace")
@@ -300,7 +322,7 @@ class HSSBatch:
             pass
 
     def factorize(self, stream=None):
-        opt = Options(HSS_FP64, 0, 0.0)
+        opt = Options(HSS_FP64, 0, 0.0, 0, 0)
         _check(load().hss_batch_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_batch_factorize")
 
