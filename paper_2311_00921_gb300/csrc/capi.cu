@@ -72,6 +72,7 @@ struct hss_s {
   double* rbuf = nullptr;              // n x kSolveCols residual
   double* bbuf = nullptr;              // n x kSolveCols copy of b (x aliasing b)
   double* norms = nullptr;             // 6 x kSolveCols: |b|, 1/|b|, |r|, 1/|r|, |x|, 1/|x|
+  double* norm_part = nullptr;         // 64 x kSolveCols partial sums of the column norms
   double* logdet_part = nullptr;       // 2^(L+1) - 1 node contributions
   double* logdet_val = nullptr;
   int* status = nullptr;
@@ -195,6 +196,7 @@ size_t layout_main(hss_s* h, char* base) {
   h->rbuf = bp.take<double>((size_t)h->n * kSolveCols);
   h->bbuf = bp.take<double>((size_t)h->n * kSolveCols);
   h->norms = bp.take<double>(6 * kSolveCols);
+  h->norm_part = bp.take<double>(64 * kSolveCols);
   h->logdet_part = bp.take<double>((size_t)(2 * nL - 1) + kRootPanels);
   h->logdet_val = bp.take<double>(1);
   h->status = bp.take<int>(8);
@@ -678,7 +680,7 @@ int matvec_pair(hss_s* h, const double* x, int ldx, double* y, int ldy, int nc, 
   double* xn = h->norms + 4 * kSolveCols;
   {
     Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
-    launch_col_norms(x, ldx, n, nc, xn, xn + kSolveCols, st);
+    launch_col_norms(x, ldx, n, nc, xn, xn + kSolveCols, h->norm_part, st);
   }
   {
     Launch k(h, HSS_K_OTHER, 0.0, st);
@@ -754,7 +756,7 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
     }
     {
       Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
-      launch_col_norms(bc, ldb, n, nc, nb, ib, st);
+      launch_col_norms(bc, ldb, n, nc, nb, ib, h->norm_part, st);
     }
     {
       Launch k(h, HSS_K_OTHER, 0.0, st);
@@ -782,7 +784,7 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
       }
       {
         Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
-        launch_col_norms(h->rbuf, n, n, nc, nr, ir, st);
+        launch_col_norms(h->rbuf, n, n, nc, nr, ir, h->norm_part, st);
       }
       if (cudaMemcpyAsync(hnr, nr, sizeof(double) * nc, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return HSS_ERR_CUDA;

@@ -50,17 +50,32 @@ __global__ void residual_kernel(const double* __restrict__ b, int ldb, double* r
 
 // norms[j] = ||v(:, j)||_2, fixed-order reduction in one CTA per column;
 // inv[j] = 1 / norms[j] (0 when the column is zero)
-__global__ void col_norms_kernel(const double* __restrict__ v, int ld, int m, double* norms,
-                                 double* inv) {
+// column norms in two fixed-order passes: kNormParts CTAs per column write
+// partial sums of squares, then one warp per column adds them in order
+constexpr int kNormParts = 64;
+
+__global__ void col_norms_part_kernel(const double* __restrict__ v, int ld, int m,
+                                      double* __restrict__ part) {
   __shared__ double red[32];
-  const int j = blockIdx.x;
+  const int j = blockIdx.y, p = blockIdx.x;
+  const int chunk = (m + kNormParts - 1) / kNormParts;
+  const int i0 = p * chunk, i1 = min(m, i0 + chunk);
   double s = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const double a = v[i + (long long)j * ld];
     s = fma(a, a, s);
   }
   s = block_sum(s, red);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) part[j * kNormParts + p] = s;
+}
+
+__global__ void col_norms_final_kernel(const double* __restrict__ part, int nc, double* norms,
+                                       double* inv) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (j >= nc) return;
+  double s = part[j * kNormParts + lane] + part[j * kNormParts + 32 + lane];
+  s = warp_sum(s);
+  if (lane == 0) {
     const double nr = sqrt(s);
     norms[j] = nr;
     if (inv) inv[j] = nr > 0.0 ? 1.0 / nr : 0.0;
@@ -106,8 +121,10 @@ void launch_residual(const double* b, int ldb, double* r, int ldr, int m, int nc
 }
 
 void launch_col_norms(const double* v, int ld, int m, int nc, double* norms, double* inv,
-                      cudaStream_t st) {
-  col_norms_kernel<<<nc, 1024, 0, st>>>(v, ld, m, norms, inv);
+                      double* scratch, cudaStream_t st) {
+  if (nc <= 0) return;
+  col_norms_part_kernel<<<dim3(kNormParts, nc), 256, 0, st>>>(v, ld, m, scratch);
+  col_norms_final_kernel<<<(nc + 7) / 8, 256, 0, st>>>(scratch, nc, norms, inv);
 }
 
 void launch_eye(double* a, int n, cudaStream_t st) {

@@ -96,34 +96,38 @@ HSS_DEVINL void cta_vt_times(const T* Pt, const T* A, long long lda, int ncols, 
   }
 }
 
-// Blocked Householder QR of the reversed basis (= QL of the basis): panels of
-// NBP columns are factored in shared memory; the trailing columns get the
-// panel's block reflector, A -= Ṽ_p (T_pᵀ (Ṽ_pᵀ A)), as two CTA-level products;
-// the compact-WY T is assembled block by block,
-// T(0:j0, p) = -T(0:j0, 0:j0) (Ṽ_{0:j0}ᵀ Ṽ_p) T_p.
-template <typename T, int NBP>
+// Blocked Householder QR of the reversed basis (= QL of the basis).  Panels of
+// NBP columns are factored in registers: thread t holds rows j0 + t + NT s of the
+// panel, and column j costs one CTA-wide reduction of the Gram row
+// g_k = Σ_{i>j} x_ij x_ik (k >= j): its first entry is the squared norm below the
+// pivot, and with the pivot row it gives every v_jᵀ x_k, so the reflector and
+// its application to the rest of the panel need no second reduction.  The
+// trailing columns get the panel's block reflector, A -= Ṽ_p (T_pᵀ (Ṽ_pᵀ A)),
+// as two CTA-level products; the compact-WY T is assembled block by block,
+// T(0:j0, p) = -T(0:j0, 0:j0) (Ṽ_{0:j0}ᵀ Ṽ_p) T_p, with T(0:j0, 0:j0) streamed
+// through shared memory in 64 x 32 slabs.
+template <typename T, int NBP, int RPT>
 __global__ void __launch_bounds__(NT)
 ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                 long long sT, T* LB, long long sL, int b, int r) {
   extern __shared__ unsigned char smem_raw[];
   T* Pt = reinterpret_cast<T*>(smem_raw);       // panel reflectors, transposed: (NBP+1) x b
-  T* P = Pt + (size_t)b * (NBP + 1);            // panel being factored, b x NBP (ld = b)
-  // after the panel factorization the P region holds the products' buffers
-  T* Ws = P;                                    // NBP x r : Ṽ_pᵀ A_trail, then T_pᵀ of it
+  T* Ws = Pt + (size_t)b * (NBP + 1);           // NBP x r : Ṽ_pᵀ A_trail
   T* Xs = Ws + (size_t)NBP * r;                 // r x NBP : Ṽ_{0:j0}ᵀ Ṽ_p
   T* Ys = Xs + (size_t)r * NBP;                 // r x NBP
   T* As = Ys + (size_t)r * NBP;                 // 64 x 33 staging slab
-  __shared__ T red[32];
+  constexpr int NW = NT / 32;
+  __shared__ T red[2][NW][NBP];
+  __shared__ T prow[2][NBP];
   __shared__ T tau_s[256];
   __shared__ T Tp[NBP][NBP + 1];
   __shared__ T Gp[NBP][NBP + 1];
-  __shared__ T beta_s;
   const long long node = blockIdx.x;
   const T* B = Bsrc + node * sB;
   T* W = V + node * sV;   // working matrix, reversed coordinates during the QR
   T* Tn = Tm + node * sT;
   T* Ln = LB + node * sL;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
   for (long long e = tid; e < (long long)b * r; e += NT) {
     const int i = (int)(e % b), j = (int)(e / b);
@@ -134,19 +138,45 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
 
   for (int j0 = 0; j0 < r; j0 += NBP) {
     const int nbw = min(NBP, r - j0);
-    for (int e = tid; e < (b - j0) * nbw; e += NT) {
-      const int i = j0 + e % (b - j0), jj = e / (b - j0);
-      P[i + jj * b] = W[i + (long long)(j0 + jj) * b];
+    T x[RPT][NBP];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      const int i = j0 + tid + NT * s;
+#pragma unroll
+      for (int k = 0; k < NBP; ++k)
+        x[s][k] = (i < b && k < nbw) ? W[i + (long long)(j0 + k) * b] : T(0);
     }
-    __syncthreads();
-    // factor the panel in shared memory
-    for (int jj = 0; jj < nbw; ++jj) {
+#pragma unroll
+    for (int jj = 0; jj < NBP; ++jj) {
+      if (jj >= nbw) break;
       const int j = j0 + jj;
-      T* pj = P + jj * b;
-      T sq = T(0);
-      for (int i = j + 1 + tid; i < b; i += NT) sq += pj[i] * pj[i];
-      const T sigma = block_sum(sq, red);
-      const T alpha = pj[j];
+      const int buf = jj & 1;
+      if (tid == jj) {   // the pivot row (row j is thread jj's first row)
+#pragma unroll
+        for (int k = 0; k < NBP; ++k) prow[buf][k] = x[0][k];
+      }
+      T g[NBP];
+#pragma unroll
+      for (int k = 0; k < NBP; ++k) g[k] = T(0);
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const int i = j0 + tid + NT * s;
+        if (i > j && i < b) {
+          const T a = x[s][jj];
+#pragma unroll
+          for (int k = jj; k < NBP; ++k) g[k] = fma(a, x[s][k], g[k]);
+        }
+      }
+      const T gw = warp_transpose_reduce<T, NBP>(g, lane);
+      if (lane < NBP) red[buf][wid][lane] = gw;
+      __syncthreads();
+      T gk = T(0);   // Σ_{i>j} x_ij x_ik for k = lane
+      if (lane < NBP) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) gk += red[buf][w][lane];
+      }
+      const T sigma = __shfl_sync(0xffffffffu, gk, jj);
+      const T alpha = prow[buf][jj];
       T tau, beta, scale;
       if (sigma == T(0)) {
         tau = T(0);
@@ -158,64 +188,105 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
         tau = (beta - alpha) / beta;
         scale = T(1) / (alpha - beta);
       }
-      if (tid == 0) {
-        tau_s[j] = tau;
-        beta_s = beta;
-      }
-      for (int i = j + 1 + tid; i < b; i += NT) pj[i] *= scale;
-      __syncthreads();
-      if (tau != T(0)) {
-        for (int kk = jj + 1 + wid; kk < nbw; kk += nw) {
-          T* pk = P + kk * b;
-          T d = T(0);
-          for (int i = j + 1 + lane; i < b; i += 32) d += pj[i] * pk[i];
-          d = warp_sum(d) + pk[j];
-          const T f = tau * d;
-          for (int i = j + 1 + lane; i < b; i += 32) pk[i] -= f * pj[i];
-          if (lane == 0) pk[j] -= f;
+      if (tid == 0) tau_s[j] = tau;
+      // v_jᵀ x_k = x_jk + scale g_k, held by lane k; then x_k -= tau (v_jᵀ x_k) v_j
+      const T tw = lane < NBP ? tau * fma(scale, gk, prow[buf][lane]) : T(0);
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const int i = j0 + tid + NT * s;
+        const bool below = i > j && i < b;
+        const T v = below ? x[s][jj] * scale : (i == j ? T(1) : T(0));
+#pragma unroll
+        for (int k = jj + 1; k < NBP; ++k) {
+          const T twk = __shfl_sync(0xffffffffu, tw, k);
+          x[s][k] = fma(-twk, v, x[s][k]);
         }
+        if (below) x[s][jj] = v;
+        if (i == j) x[s][jj] = beta;   // R(j, j)
       }
-      __syncthreads();
-      if (tid == 0) pj[j] = beta_s;   // R(j, j)
-      __syncthreads();
     }
     // write the panel back (R on and above the diagonal, reflectors below) and
     // keep the reflectors, with their unit diagonal and zeros above, transposed
-    for (int e = tid; e < (b - j0) * nbw; e += NT) {
-      const int i = j0 + e % (b - j0), jj = e / (b - j0);
-      W[i + (long long)(j0 + jj) * b] = P[i + jj * b];
-    }
-    for (int e = tid; e < b * NBP; e += NT) {
-      const int i = e / NBP, q = e % NBP;
-      const int d = j0 + q;
-      T v = T(0);
-      if (q < nbw && i >= j0) v = i > d ? P[i + q * b] : (i == d ? T(1) : T(0));
-      Pt[q + i * (NBP + 1)] = v;
-    }
-    __syncthreads();
-    // panel Gram Gp(a, c) = v_aᵀ v_c (a < c) and panel T (forward dlarft)
-    for (int pr = wid; pr < nbw * nbw; pr += nw) {
-      const int a = pr % nbw, c = pr / nbw;
-      if (a >= c) continue;
-      T d = T(0);
-      for (int i = j0 + c + lane; i < b; i += 32)
-        d += Pt[a + i * (NBP + 1)] * Pt[c + i * (NBP + 1)];
-      d = warp_sum(d);
-      if (lane == 0) Gp[a][c] = d;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      for (int c = 0; c < nbw; ++c) {
-        T v = T(0);
-        if (lane < c) {
-          for (int m = lane; m < c; ++m) v += Tp[lane][m] * Gp[m][c];
-          v = -tau_s[j0 + c] * v;
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      const int i = j0 + tid + NT * s;
+      if (i < b) {
+#pragma unroll
+        for (int k = 0; k < NBP; ++k) {
+          if (k < nbw) W[i + (long long)(j0 + k) * b] = x[s][k];
+          const int d = j0 + k;
+          T v = T(0);
+          if (k < nbw) v = i > d ? x[s][k] : (i == d ? T(1) : T(0));
+          Pt[k + i * (NBP + 1)] = v;
         }
-        __syncwarp();
-        if (lane < c) Tp[lane][c] = v;
-        if (lane == c) Tp[c][c] = tau_s[j0 + c];
-        if (lane > c && lane < NBP) Tp[lane][c] = T(0);
-        __syncwarp();
+      }
+    }
+    for (int e = tid; e < j0 * NBP; e += NT) Pt[(e % NBP) + (e / NBP) * (NBP + 1)] = T(0);
+    __syncthreads();
+    // panel Gram Gp(a, c) = v_aᵀ v_c (a < c) from the register panel: the
+    // columns c and NBP - c share one transposing warp reduction (c + (NBP - c)
+    // = NBP products), then the warps' partials are summed through shared memory
+    {
+      T* Gs = Ws;   // NW x NBP x (NBP + 1) partials; the product buffers are free here
+#pragma unroll
+      for (int c = 1; c <= NBP / 2; ++c) {
+        const int c2 = NBP - c;   // partner column (c2 == c for c = NBP / 2)
+        T g[NBP];
+#pragma unroll
+        for (int q = 0; q < NBP; ++q) g[q] = T(0);
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+          const int i = j0 + tid + NT * s;
+          if (i < b) {
+            auto vref = [&](int k) -> T {
+              const int d = j0 + k;
+              return i > d ? x[s][k] : (i == d ? T(1) : T(0));
+            };
+            const T vc = vref(c), vc2 = vref(c2);
+#pragma unroll
+            for (int q = 0; q < NBP; ++q) {
+              if (q < c) g[q] = fma(vref(q), vc, g[q]);                   // (a = q, c)
+              else if (c2 != c) g[q] = fma(vref(q - c), vc2, g[q]);       // (a = q - c, c2)
+            }
+          }
+        }
+        const T gw = warp_transpose_reduce<T, NBP>(g, lane);
+        if (lane < NBP) {
+          if (lane < c) Gs[(wid * NBP + c) * (NBP + 1) + lane] = gw;
+          else if (c2 != c && lane - c < c2) Gs[(wid * NBP + c2) * (NBP + 1) + (lane - c)] = gw;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < NBP * NBP; e += NT) {
+        const int a = e % NBP, c = e / NBP;
+        if (a < c) {
+          T v = T(0);
+#pragma unroll
+          for (int w = 0; w < NW; ++w) v += Gs[(w * NBP + c) * (NBP + 1) + a];
+          Gp[a][c] = v;
+        }
+      }
+      __syncthreads();
+    }
+    // panel T (forward dlarft): T_p(0:c, c) = -tau_c T_p(0:c, 0:c) Gp(0:c, c),
+    // lane a keeps row a of T_p in registers
+    if (wid == 0) {
+      T tp[NBP];
+#pragma unroll
+      for (int m = 0; m < NBP; ++m) tp[m] = T(0);
+#pragma unroll
+      for (int c = 0; c < NBP; ++c) {
+        if (c < nbw) {
+          const T tc = tau_s[j0 + c];
+          T v = T(0);
+#pragma unroll
+          for (int m = 0; m < c; ++m) v = fma(tp[m], Gp[m][c], v);
+          tp[c] = lane < c ? -tc * v : (lane == c ? tc : T(0));
+        }
+      }
+      if (lane < NBP) {
+#pragma unroll
+        for (int m = 0; m < NBP; ++m) Tp[lane][m] = (lane < nbw && m < nbw) ? tp[m] : T(0);
       }
     }
     __syncthreads();
@@ -223,14 +294,39 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
     if (j0 > 0) {
       // Xs(a, q) = v_aᵀ v_q over rows >= j0 (where v_a, a < j0, is below its diagonal)
       cta_vt_times<T, NBP>(Pt, W, b, j0, j0, b, As, Xs, 1, NBP);
-    }
-    __syncthreads();
-    if (j0 > 0) {
-      for (int e = tid; e < j0 * nbw; e += NT) {   // Y = T(0:j0, 0:j0) X
-        const int a = e % j0, q = e / j0;
-        T v = T(0);
-        for (int m = a; m < j0; ++m) v += Tn[a + (long long)m * r] * Xs[q + m * NBP];
-        Ys[a + q * r] = v;
+      __syncthreads();
+      // Ys(a, q) = Σ_{m >= a} T(a, m) Xs(m, q): thread owns row a0 + tid % 64 and
+      // columns tid / 64 + (NT / 64) t of each 64-row block
+      constexpr int QT = NBP / (NT / 64);
+      const int aa = tid % 64, qb = tid / 64;
+      for (int a0 = 0; a0 < j0; a0 += 64) {
+        T acc[QT];
+#pragma unroll
+        for (int t = 0; t < QT; ++t) acc[t] = T(0);
+        for (int m0 = a0; m0 < j0; m0 += 32) {
+          for (int e = tid; e < 64 * 32; e += NT) {
+            const int ra = e % 64, mm = e / 64;
+            const int ga = a0 + ra, gm = m0 + mm;
+            As[ra * 33 + mm] = (ga < j0 && gm < j0) ? Tn[ga + (long long)gm * r] : T(0);
+          }
+          __syncthreads();
+          for (int mm = 0; mm < 32; ++mm) {
+            const T tv = As[aa * 33 + mm];
+            const int m = m0 + mm;
+            if (m >= j0) break;
+#pragma unroll
+            for (int t = 0; t < QT; ++t) acc[t] = fma(tv, Xs[(qb + (NT / 64) * t) + m * NBP], acc[t]);
+          }
+          __syncthreads();
+        }
+        const int a = a0 + aa;
+        if (a < j0) {
+#pragma unroll
+          for (int t = 0; t < QT; ++t) {
+            const int q = qb + (NT / 64) * t;
+            if (q < nbw) Ys[a + q * r] = acc[t];
+          }
+        }
       }
       __syncthreads();
       for (int e = tid; e < j0 * nbw; e += NT) {   // T(0:j0, panel) = -Y T_p
@@ -281,27 +377,21 @@ ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, lon
     __syncthreads();
   }
 
-  // L_B(a, c) = R(r-1-a, r-1-c): R is the upper triangle of W
-  for (int e = tid; e < r * r; e += NT) {
-    const int a = e % r, c = e / r;
-    T v = T(0);
-    if (a >= c) v = W[(r - 1 - a) + (long long)(r - 1 - c) * b];
-    Ln[a + (long long)c * r] = v;
-  }
-  __syncthreads();
-  // explicit unit diagonal and zeros above it in the reversed reflectors
-  for (int e = tid; e < r * r; e += NT) {
-    const int i = e % r, j = e / r;
-    if (i <= j) W[i + (long long)j * b] = (i == j) ? T(1) : T(0);
-  }
-  __syncthreads();
-  // back to natural row order: V = F_b Ṽ
-  for (long long e = tid; e < (long long)(b / 2) * r; e += NT) {
-    const int i = (int)(e % (b / 2)), j = (int)(e / (b / 2));
-    T* col = W + (long long)j * b;
-    const T x = col[i];
-    col[i] = col[b - 1 - i];
-    col[b - 1 - i] = x;
+  // One pass over row pairs (i, b-1-i) of the reversed working matrix: L_B(a, c)
+  // = R(r-1-a, r-1-c) from its upper triangle, and V = F_b Ṽ with Ṽ's unit
+  // diagonal and zeros above written in, each pair read and written by one thread.
+  const int half = (b + 1) / 2;
+  for (long long e = tid; e < (long long)half * r; e += NT) {
+    const int i = (int)(e % half), j = (int)(e / half);
+    const int i2 = b - 1 - i;
+    const T w1 = W[i + (long long)j * b];
+    const T w2 = W[i2 + (long long)j * b];
+    if (i < r) Ln[(r - 1 - i) + (long long)(r - 1 - j) * r] = i <= j ? w1 : T(0);
+    if (i2 != i && i2 < r) Ln[(r - 1 - i2) + (long long)(r - 1 - j) * r] = i2 <= j ? w2 : T(0);
+    const T v1 = i > j ? w1 : (i == j ? T(1) : T(0));     // Ṽ(i, j)  -> V(b-1-i, j)
+    const T v2 = i2 > j ? w2 : (i2 == j ? T(1) : T(0));   // Ṽ(i2, j) -> V(i, j)
+    W[i + (long long)j * b] = v2;
+    if (i2 != i) W[i2 + (long long)j * b] = v1;
   }
 }
 
@@ -538,31 +628,76 @@ chol_panel_kernel(T* Mb, int ldm, long long sM, int rows, int kb, double* logdet
 }
 
 // ------------------------------------------------------------------ triangular sweeps
+// Both sweeps walk the factored columns in blocks of CB (<= NB): the block's
+// panel (rows k0 .. b-1 of columns k0 .. k0+kb-1, the diagonal block and the
+// L^RR / L^SR rows below it) is staged into shared memory with cp.async, the
+// next block's copy in flight while the current one is used (NBUF = 2), so the
+// global-memory latency stays out of the dependent chains.  Panel pitch P = b|1
+// (odd) keeps both row-wise and column-wise lane access free of bank conflicts.
+HSS_DEVINL uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+HSS_DEVINL void cp_async_elem(float* s, const float* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+HSS_DEVINL void cp_async_elem(double* s, const double* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+HSS_DEVINL void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+HSS_DEVINL void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// rows k0 .. b-1 of columns k0 .. k0+kb-1 of M into Lp (pitch P), one commit group
+template <typename T>
+HSS_DEVINL void stage_panel(const T* M, int ldm, int k0, int kb, int b, T* Lp, int P) {
+  const int n1 = b - k0;
+  for (int e = threadIdx.x; e < n1 * kb; e += NT) {
+    const int ii = e % n1, t = e / n1;
+    cp_async_elem(Lp + ii + t * P, M + (k0 + ii) + (long long)(k0 + t) * ldm);
+  }
+  cp_async_commit();
+}
+
 // forward: y (b x nrhs, smem) := [L^RR⁻¹ y^R ; y^S - L^SR L^RR⁻¹ y^R]
 template <typename T>
 __global__ void __launch_bounds__(NT)
 trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
-                long long sX, int nrhs, T* Par, int ldpar, long long sPar) {
-  extern __shared__ unsigned char smem_raw[];
+                long long sX, int nrhs, T* Par, int ldpar, long long sPar, int CB, int NBUF) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs, ld = b
+  const int P = b | 1;
+  T* Lbuf = y + (size_t)b * nrhs;          // NBUF panels of P x CB
   const int node = blockIdx.x;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
+  const int nblk = (c + CB - 1) / CB;
+  if (nblk > 0) stage_panel(M, ldm, 0, min(CB, c), b, Lbuf, P);
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     y[i + j * b] = x[i + (long long)j * ldx];
   }
-  __syncthreads();
-  for (int k0 = 0; k0 < c; k0 += NB) {
-    const int kb = min(NB, c - k0);
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int k0 = bi * CB;
+    const int kb = min(CB, c - k0);
+    const T* L = Lbuf + (size_t)(NBUF == 2 ? (bi & 1) : 0) * P * CB;
+    const bool next = bi + 1 < nblk;
+    if (NBUF == 2 && next) {
+      stage_panel(M, ldm, k0 + CB, min(CB, c - k0 - CB), b, Lbuf + (size_t)((bi + 1) & 1) * P * CB,
+                  P);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
     // diagonal block: warp w handles right-hand sides w, w + nw, ...; lane i
-    // keeps row i of the block in registers (loaded once, outside the chain)
+    // keeps row i of the block in registers
     {
       T lrow[NB];
 #pragma unroll
-      for (int t = 0; t < NB; ++t)
-        lrow[t] = (lane < kb && t <= lane) ? M[(k0 + lane) + (long long)(k0 + t) * ldm] : T(0);
+      for (int t = 0; t < NB; ++t) lrow[t] = (lane < kb && t <= lane) ? L[lane + t * P] : T(0);
       const T inv = lane < kb ? T(1) / reg_select(lrow, lane) : T(0);
       for (int j = wid; j < nrhs; j += nw) {
         T* yj = y + j * b + k0;
@@ -578,23 +713,29 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       }
     }
     __syncthreads();
-    // update every row below the block (the S rows included: L^SR lives there)
+    // every row below the block (the S rows included: L^SR lives there)
     for (int i = k0 + kb + tid; i < b; i += NT) {
+      const int ii = i - k0;
       T acc[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) acc[j] = T(0);
-      for (int t = 0; t < kb; ++t) {
-        const T l = M[i + (long long)(k0 + t) * ldm];
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (j < nrhs) acc[j] = fma(l, y[(k0 + t) + j * b], acc[j]);
+      for (int t = 0; t < NB; ++t) {
+        if (t < kb) {
+          const T l = L[ii + t * P];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j < nrhs) acc[j] = fma(l, y[(k0 + t) + j * b], acc[j]);
+        }
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         if (j < nrhs) y[i + j * b] -= acc[j];
     }
     __syncthreads();
+    if (NBUF == 1 && next) stage_panel(M, ldm, k0 + CB, min(CB, c - k0 - CB), b, Lbuf, P);
   }
+  cp_async_wait<0>();
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     x[i + (long long)j * ldx] = y[i + j * b];
@@ -614,14 +755,22 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
 template <typename T>
 __global__ void __launch_bounds__(NT)
 trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
-                long long sX, int nrhs, const T* Par, int ldpar, long long sPar) {
-  extern __shared__ unsigned char smem_raw[];
+                long long sX, int nrhs, const T* Par, int ldpar, long long sPar, int CB,
+                int NBUF) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs
+  const int P = b | 1;
+  T* Lbuf = y + (size_t)b * nrhs;
   const int node = blockIdx.x;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
-  const int r = b - c;
+  const int nblk = (c + CB - 1) / CB;
+  if (nblk > 0) {
+    const int k0 = (nblk - 1) * CB;
+    stage_panel(M, ldm, k0, c - k0, b, Lbuf + (size_t)(NBUF == 2 ? ((nblk - 1) & 1) : 0) * P * CB,
+                P);
+  }
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     T v;
@@ -631,30 +780,31 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       v = x[i + (long long)j * ldx];
     y[i + j * b] = v;
   }
-  __syncthreads();
-  const int nblk = (c + NB - 1) / NB;
   for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int k0 = bi * NB;
-    const int kb = min(NB, c - k0);
-    // z_t -= sum_{i >= k0+kb} L(i, t) x_i for t in the block: one warp per t,
-    // lanes over i, every right-hand side at once, then warp reductions
-    for (int t = wid; t < kb; t += nw) {
-      const T* lcol = M + (long long)(k0 + t) * ldm;
-      T acc[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = T(0);
-      for (int i = k0 + kb + lane; i < b; i += 32) {
-        const T l = lcol[i];
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (j < nrhs) acc[j] = fma(l, y[i + j * b], acc[j]);
+    const int k0 = bi * CB;
+    const int kb = min(CB, c - k0);
+    const T* L = Lbuf + (size_t)(NBUF == 2 ? (bi & 1) : 0) * P * CB;
+    const bool next = bi > 0;
+    if (NBUF == 2 && next) {
+      stage_panel(M, ldm, k0 - CB, CB, b, Lbuf + (size_t)((bi - 1) & 1) * P * CB, P);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // z_t -= Σ_{i >= k0+kb} L(i, t) x_i: thread (t = lane, j = warp, warp + nw)
+    // runs two dependent chains down the rows
+    if (lane < kb) {
+      const int t = lane;
+      const int j0 = wid, j1 = wid + nw;
+      T a0 = T(0), a1 = T(0);
+      for (int i = k0 + kb; i < b; ++i) {
+        const T l = L[(i - k0) + t * P];
+        if (j0 < nrhs) a0 = fma(l, y[i + j0 * b], a0);
+        if (j1 < nrhs) a1 = fma(l, y[i + j1 * b], a1);
       }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (j >= nrhs) break;
-        const T sum = warp_sum(acc[j]);
-        if (lane == 0) y[(k0 + t) + j * b] -= sum;
-      }
+      if (j0 < nrhs) y[(k0 + t) + j0 * b] -= a0;
+      if (j1 < nrhs) y[(k0 + t) + j1 * b] -= a1;
     }
     __syncthreads();
     // diagonal block, transposed back substitution; lane i keeps column i of
@@ -663,8 +813,7 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       T lcol[NB];
 #pragma unroll
       for (int t = 0; t < NB; ++t)
-        lcol[t] = (lane < kb && t >= lane && t < kb) ? M[(k0 + t) + (long long)(k0 + lane) * ldm]
-                                                      : T(0);
+        lcol[t] = (lane < kb && t >= lane && t < kb) ? L[t + lane * P] : T(0);
       const T inv = lane < kb ? T(1) / reg_select(lcol, lane) : T(0);
       for (int j = wid; j < nrhs; j += nw) {
         T* yj = y + j * b + k0;
@@ -680,8 +829,9 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       }
     }
     __syncthreads();
+    if (NBUF == 1 && next) stage_panel(M, ldm, k0 - CB, CB, b, Lbuf, P);
   }
-  (void)r;
+  cp_async_wait<0>();
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     x[i + (long long)j * ldx] = y[i + j * b];
@@ -726,20 +876,36 @@ bool smem_opt_in(K kernel, size_t bytes) {
 template <typename T>
 size_t ql_smem(int b, int r) {
   constexpr int NBP = sizeof(T) == 8 ? 16 : 32;
-  const size_t region = std::max<size_t>((size_t)b * NBP, (size_t)3 * NBP * r + 64 * 33);
+  // transposed panel, then the product buffers (which also hold the warps'
+  // partial panel Gram matrices)
+  const size_t region = std::max<size_t>((size_t)3 * NBP * r + 64 * 33,
+                                         (size_t)(NT / 32) * NBP * (NBP + 1));
   return ((size_t)b * (NBP + 1) + region) * sizeof(T);
+}
+
+template <typename T, int NBP, int RPT>
+cudaError_t launch_ql_rows(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
+                           long long sT, T* LB, long long sL, int b, int r, int nodes,
+                           cudaStream_t st) {
+  const size_t sm = ql_smem<T>(b, r);
+  if (!smem_opt_in(ql_basis_kernel<T, NBP, RPT>, sm)) return cudaErrorInvalidConfiguration;
+  ql_basis_kernel<T, NBP, RPT><<<nodes, NT, sm, st>>>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL,
+                                                      b, r);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                             long long sT, T* LB, long long sL, int b, int r, int nodes,
                             cudaStream_t st) {
-  // panel width: 16 columns in FP64, 32 in FP32 (the panel lives in shared memory)
+  // panel width: 16 columns in FP64, 32 in FP32; RPT panel rows per thread
   constexpr int NBP = sizeof(T) == 8 ? 16 : 32;
-  const size_t sm = ql_smem<T>(b, r);
-  if (!smem_opt_in(ql_basis_kernel<T, NBP>, sm)) return cudaErrorInvalidConfiguration;
-  ql_basis_kernel<T, NBP><<<nodes, NT, sm, st>>>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r);
-  return cudaGetLastError();
+  if (b > 3 * NT || r > 256) return cudaErrorInvalidValue;
+  if (b <= NT)
+    return launch_ql_rows<T, NBP, 1>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st);
+  if (b <= 2 * NT)
+    return launch_ql_rows<T, NBP, 2>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st);
+  return launch_ql_rows<T, NBP, 3>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st);
 }
 
 template <typename T>
@@ -775,8 +941,10 @@ __global__ void scatter_ss_kernel(const T* __restrict__ Mb, int ldm, long long s
   const T* M = Mb + (long long)node * sM;
   T* A = PA + (long long)(node >> 1) * sPA;
   const int off = (node & 1) * r;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int i = e % r, j = e / r;
+  // CTA y takes columns y, y + gridDim.y, ...
+  const int ncol = (r - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y;
+  for (int e = threadIdx.x; e < r * ncol; e += blockDim.x) {
+    const int i = e % r, j = (int)blockIdx.y + (e / r) * (int)gridDim.y;
     if (i < j) continue;
     const T v = M[(c + i) + (long long)(c + j) * ldm];
     A[(off + i) + (long long)(off + j) * ldpa] = v;
@@ -787,17 +955,43 @@ __global__ void scatter_ss_kernel(const T* __restrict__ Mb, int ldm, long long s
 template <typename T>
 cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T* PA, int ldpa,
                               long long sPA, int nodes, cudaStream_t st) {
-  scatter_ss_kernel<T><<<nodes, NT, 0, st>>>(M, ldm, sM, c, r, PA, ldpa, sPA);
+  if (r <= 0 || nodes <= 0) return cudaSuccess;
+  scatter_ss_kernel<T><<<dim3(nodes, std::min(r, 16)), NT, 0, st>>>(M, ldm, sM, c, r, PA, ldpa,
+                                                                    sPA);
   return cudaGetLastError();
+}
+
+// shared memory of a sweep: the node vector plus NBUF staged panels of P x CB
+template <typename T>
+size_t trsv_smem(int b, int nrhs, int CB, int NBUF) {
+  return ((size_t)b * nrhs + (size_t)NBUF * (b | 1) * CB) * sizeof(T);
+}
+
+// the largest staging the device allows: two 32-column panels, else one, else
+// 16- and 8-column panels
+template <typename T, typename K>
+cudaError_t trsv_config(K kernel, int b, int nrhs, int* CB, int* NBUF, size_t* sm) {
+  const int cbs[4] = {32, 32, 16, 8}, bufs[4] = {2, 1, 1, 1};
+  for (int q = 0; q < 4; ++q) {
+    *CB = cbs[q];
+    *NBUF = bufs[q];
+    *sm = trsv_smem<T>(b, nrhs, *CB, *NBUF);
+    if (smem_opt_in(kernel, *sm)) return cudaSuccess;
+  }
+  return cudaErrorInvalidConfiguration;
 }
 
 template <typename T>
 cudaError_t launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                             long long sX, int nrhs, T* Par, int ldpar, long long sPar, int nodes,
                             cudaStream_t st) {
-  const size_t sm = (size_t)b * nrhs * sizeof(T);
-  if (!smem_opt_in(trsv_fwd_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
-  trsv_fwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar);
+  if (nrhs > 16) return cudaErrorInvalidValue;
+  int CB, NBUF;
+  size_t sm;
+  cudaError_t e = trsv_config<T>(trsv_fwd_kernel<T>, b, nrhs, &CB, &NBUF, &sm);
+  if (e != cudaSuccess) return e;
+  trsv_fwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar,
+                                            CB, NBUF);
   return cudaGetLastError();
 }
 
@@ -805,9 +999,13 @@ template <typename T>
 cudaError_t launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                             long long sX, int nrhs, const T* Par, int ldpar, long long sPar,
                             int nodes, cudaStream_t st) {
-  const size_t sm = (size_t)b * nrhs * sizeof(T);
-  if (!smem_opt_in(trsv_bwd_kernel<T>, sm)) return cudaErrorInvalidConfiguration;
-  trsv_bwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar);
+  if (nrhs > 16) return cudaErrorInvalidValue;
+  int CB, NBUF;
+  size_t sm;
+  cudaError_t e = trsv_config<T>(trsv_bwd_kernel<T>, b, nrhs, &CB, &NBUF, &sm);
+  if (e != cudaSuccess) return e;
+  trsv_bwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar,
+                                            CB, NBUF);
   return cudaGetLastError();
 }
 
