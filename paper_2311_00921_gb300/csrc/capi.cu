@@ -320,19 +320,27 @@ void apply_q(hss_s* h, Factor<T>& f, const LevelT<T>& P, T* vec, int ldv, int nc
           b, n, st);
 }
 
+enum { SPLIT_D = 1, SPLIT_U = 2, SPLIT_E = 4, SPLIT_S = 8, SPLIT_ALL = 15 };
+cudaError_t split_generators(hss_s* h, cudaStream_t st, int which);
+
 // levels L .. 1 of Alg. 2; leaves the merged root block in f.lv[0].A.
 // Two chains: the basis chain (basis completion of level l, then the merge's
 // rescaled coupling Ŝ and the parent basis, which need only L_B of level l) runs
 // ahead on h->qstream; the main chain (diagonal product and partial Cholesky of
 // level l) waits for level l's basis event.  The levels' basis completions,
-// latency-bound at the top of the tree, thus overlap the main chain.
+// latency-bound at the top of the tree, thus overlap the main chain.  With
+// split_d the FP32 copy of D is made on the main chain once the basis chain has
+// started (only the leaves' diagonal product needs it).
 template <typename T>
-int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st) {
+int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) {
   const int L = h->L, r = h->rank;
   const long long rr = (long long)r * r;
   cudaStream_t qs = h->qstream;
   if (cudaEventRecord(h->ev_start, st) != cudaSuccess) return HSS_ERR_CUDA;
   if (cudaStreamWaitEvent(qs, h->ev_start, 0) != cudaSuccess) return HSS_ERR_CUDA;
+  if constexpr (std::is_same<T, float>::value) {
+    if (split_d && split_generators(h, st, SPLIT_D) != cudaSuccess) return HSS_ERR_CUDA;
+  }
   // basis chain
   for (int l = L; l >= 1; --l) {
     LevelT<T>& P = f.lv[l];
@@ -419,7 +427,7 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st) {
       T* Mk = P.M + k0 + (long long)k0 * b;
       {
         Launch k(h, HSS_K_PCHOL, panel_flops(rows, kb) * n, st, sizeof(T) == 4);
-        HSS_TRY(launch_chol_panel<T>(Mk, b, bb, rows, kb, slots, l, k0, h->status, n, k0 > 0,
+        HSS_TRY(launch_chol_panel<T>(Mk, b, bb, rows, kb, slots, l, 0, k0, h->status, n, k0 > 0,
                                      st));
       }
       if (nt > 0) {
@@ -452,7 +460,7 @@ int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
     double* Mk = R + k0 + (long long)k0 * b0;
     {
       Launch k(h, HSS_K_PCHOL, panel_flops(rows, kb), st);
-      HSS_TRY(launch_chol_panel<double>(Mk, b0, 0, rows, kb, slots + p, 0, k0, h->status, 1,
+      HSS_TRY(launch_chol_panel<double>(Mk, b0, 0, rows, kb, slots + p, 0, 0, k0, h->status, 1,
                                         false, st));
     }
     const int nt = rows - kb;
@@ -465,23 +473,23 @@ int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
   return check_launch();
 }
 
-cudaError_t split_generators(hss_s* h, cudaStream_t st);
-
 int factorize(hss_s* h, int prec, cudaStream_t st) {
   const int L = h->L, r = h->rank;
   cudaMemsetAsync(h->status, 0, 8 * sizeof(int), st);
   double* root = nullptr;
   if (prec == HSS_FP64) {
-    int rc = factor_levels<double>(h, h->f64, h->zq64, st);
+    int rc = factor_levels<double>(h, h->f64, h->zq64, st, false);
     if (rc) return rc;
     root = h->f64.lv[0].A;
   } else {
     Factor<float>& f = h->f32;
     // the generators in FP32 (part of every factorization), with their
-    // low-order FP32 parts for the pair-arithmetic residual
-    HSS_TRY(split_generators(h, st));
-    int rc = factor_levels<float>(h, f, h->zq32, st);
+    // low-order FP32 parts for the pair-arithmetic residual: U, E and S before
+    // the basis chain starts, D (the large one) on the main chain after it
+    HSS_TRY(split_generators(h, st, SPLIT_U | SPLIT_E | SPLIT_S));
+    int rc = factor_levels<float>(h, f, h->zq32, st, /*split_d=*/true);
     if (rc) return rc;
+    h->pairs_valid = 1;
     {   // the root block goes to FP64 for the root Cholesky
       Launch k(h, HSS_K_OTHER, 0.0, st);
       launch_f32_to_f64(f.lv[0].A, h->R0, 4LL * r * r, st);
@@ -621,29 +629,30 @@ int matvec_fp64(hss_s* h, const double* x, int ldx, double* y, int ldy, int nrhs
   return HSS_OK;
 }
 
-// hi = fl32(g) into the FP32 factor's generator copies, lo = fl32(g - hi)
-cudaError_t split_generators(hss_s* h, cudaStream_t st) {
+// hi = fl32(g) into the FP32 factor's generator copies, lo = fl32(g - hi);
+// `which` selects D, U, E, S (SPLIT_*)
+cudaError_t split_generators(hss_s* h, cudaStream_t st, int which) {
   const int L = h->L, r = h->rank;
   Factor<float>& f = h->f32;
   const long long nL = 1LL << L;
   cudaError_t e = cudaSuccess;
-  {
+  if (which & SPLIT_D) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
     e = launch_df_split(h->D, f.Dc, h->Dl, nL * h->leaf * h->leaf, st);
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && (which & SPLIT_U)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
     e = launch_df_split(h->U, f.Uc, h->Ul, nL * h->leaf * r, st);
   }
-  if (e == cudaSuccess && h->esz) {
+  if (e == cudaSuccess && h->esz && (which & SPLIT_E)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
     e = launch_df_split(h->E, f.Ec, h->El, h->esz, st);
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && (which & SPLIT_S)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
     e = launch_df_split(h->S, f.Sc, h->Sl, h->ssz, st);
   }
-  if (e == cudaSuccess) h->pairs_valid = 1;
+  if (e == cudaSuccess && which == SPLIT_ALL) h->pairs_valid = 1;
   return e;
 }
 
@@ -969,7 +978,7 @@ int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t l
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->last_stream = st;
-  if (!h->pairs_valid && split_generators(h, st) != cudaSuccess) return HSS_ERR_CUDA;
+  if (!h->pairs_valid && split_generators(h, st, SPLIT_ALL) != cudaSuccess) return HSS_ERR_CUDA;
   for (int j0 = 0; j0 < nrhs; j0 += kSolveCols) {
     const int nc = std::min(kSolveCols, nrhs - j0);
     rc = matvec_pair(h, x + (long long)j0 * ld, ld, y + (long long)j0 * ld, ld, nc, st);

@@ -557,7 +557,7 @@ HSS_DEVINL T reg_select(const T (&a)[NB], int i) {
 template <typename T>
 __global__ void __launch_bounds__(NT)
 chol_panel_kernel(T* Mb, int ldm, long long sM, int rows, int kb, double* logdet_part, int level,
-                  int col0, int* status, int accumulate) {
+                  int node0, int col0, int* status, int accumulate) {
   __shared__ T Ls[NB][NB + 1];   // Ls[t][j] = L(t, j) of the diagonal block
   __shared__ T dinv[NB];
   __shared__ int fail;
@@ -588,7 +588,7 @@ chol_panel_kernel(T* Mb, int ldm, long long sM, int rows, int kb, double* logdet
     }
     if (lane == 0) fail = bad >= 0;
     if (bad >= 0) {
-      if (lane == 0) report_failure(status, -3 /*NOT_SPD*/, level, node, col0 + bad);
+      if (lane == 0) report_failure(status, -3 /*NOT_SPD*/, level, node0 + node, col0 + bad);
     } else {
 #pragma unroll
       for (int t = 0; t < NB; ++t)
@@ -924,10 +924,10 @@ cudaError_t launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int l
 
 template <typename T>
 cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, double* logdet_part,
-                              int level, int col0, int* status, int nodes, bool accumulate,
-                              cudaStream_t st) {
+                              int level, int node0, int col0, int* status, int nodes,
+                              bool accumulate, cudaStream_t st) {
   if (kb < 1 || kb > NB || rows < kb) return cudaErrorInvalidValue;
-  chol_panel_kernel<T><<<nodes, NT, 0, st>>>(M, ldm, sM, rows, kb, logdet_part, level, col0,
+  chol_panel_kernel<T><<<nodes, NT, 0, st>>>(M, ldm, sM, rows, kb, logdet_part, level, node0, col0,
                                              status, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
@@ -1023,7 +1023,7 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
   template cudaError_t launch_trsv_bwd<T>(const T*, int, long long, int, int, T*, int, long long, \
                                           int, const T*, int, long long, int, cudaStream_t);      \
   template size_t ql_smem<T>(int, int);                                                          \
-  template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int,     \
+  template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int, int,\
                                             int*, int, bool, cudaStream_t);                       \
   template cudaError_t launch_scatter_ss<T>(const T*, int, long long, int, int, T*, int,           \
                                             long long, int, cudaStream_t);

@@ -35,8 +35,8 @@ size_t ql_smem(int b, int r);
 // Writes (or, with accumulate, adds) 2 Σ log diag to logdet_part[node].
 template <typename T>
 cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, double* logdet_part,
-                              int level, int col0, int* status, int nodes, bool accumulate,
-                              cudaStream_t st);
+                              int level, int node0, int col0, int* status, int nodes,
+                              bool accumulate, cudaStream_t st);
 
 // The merge of Alg. 2 line 4 as its own pass: Â^SS of node i (lower triangle
 // of M[c:, c:], r x r) into block (i & 1) of parent i / 2's diagonal, both triangles.

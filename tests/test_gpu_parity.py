@@ -177,6 +177,35 @@ def test_not_spd_reports_level_and_node():
     assert (eo.value.level, eo.value.node, eo.value.col) == (3, 5, info["col"])
 
 
+def test_six_levels_fp64_and_mixed():
+    """64 leaves of 40 (six levels, blocked Cholesky over 1-2 panels per node):
+    per-step arrays, x and log det against the oracle in FP64, and the FP32
+    factor under pair-residual refinement to a 1e-12 residual."""
+    h = I.random_hss(6, 40, 8, seed=31, orthonormal=False)
+    dev, F, b, x = run_both(h, 3)
+    check_steps(dev, F, h)
+    check_end_to_end(dev, F, b, x)
+    dev.factorize("fp32", residual="pair32")
+    x32 = dev.solve(hss.colmajor(b)).cpu().numpy()
+    res = b - O.matvec(h, x32)
+    assert (np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)).max() <= 1e-12
+
+
+def test_not_spd_reports_a_late_leaf():
+    h = I.random_hss(6, 40, 8, seed=32)
+    h.D[37] = -h.D[37]
+    dev = hss.HSS(h)
+    dev.factorize("fp64")
+    with pytest.raises(hss.HSSError) as ei:
+        dev.logdet()
+    assert ei.value.code == -3
+    info = dev.last_info()
+    assert info["level"] == 6 and info["node"] == 37
+    with pytest.raises(O.NotSPD) as eo:
+        O.factor(h)
+    assert (eo.value.level, eo.value.node, eo.value.col) == (6, 37, info["col"])
+
+
 def test_solve_before_factorize():
     h = I.random_hss(2, 32, 4, seed=1)
     dev = hss.HSS(h)
