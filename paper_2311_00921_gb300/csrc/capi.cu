@@ -28,7 +28,8 @@ namespace {
 constexpr int kMaxCols = 32;      // right-hand-side columns per matvec pass
 constexpr int kSolveCols = 16;    // columns per triangular-sweep / refinement pass
 constexpr int kPanel = 32;        // columns per blocked-Cholesky panel (the panel kernel's limit)
-constexpr int kRootPanels = 16;   // log-det slots of the blocked root Cholesky (2r <= 512)
+constexpr int kRootPanels = 16;
+constexpr int kFuseNodes = 64;     // levels up to this many nodes apply Q inside the sweep kernel   // log-det slots of the blocked root Cholesky (2r <= 512)
 
 template <typename T>
 struct LevelT {
@@ -45,7 +46,8 @@ struct LevelT {
 template <typename T>
 struct Factor {
   std::vector<LevelT<T>> lv;   // index = level (0 = root)
-  T *W = nullptr, *Y = nullptr, *X = nullptr, *Z = nullptr, *t1 = nullptr, *t2 = nullptr;
+  T *W = nullptr, *Y = nullptr, *X = nullptr, *Z = nullptr;
+  T *t1 = nullptr, *t2 = nullptr;   // r x kSolveCols per node: Q application of wide levels
   const T *D = nullptr, *U = nullptr, *E = nullptr, *S = nullptr;   // generators in T
   T *Dc = nullptr, *Uc = nullptr, *Ec = nullptr, *Sc = nullptr;     // converted copies (float)
   T* d = nullptr;               // n x kSolveCols refinement correction (float)
@@ -153,8 +155,8 @@ void layout_factor(Bump& bp, Factor<T>& f, int L, int leaf, int r) {
   f.Y = bp.take<T>(nL * leaf * r);
   f.X = bp.take<T>(nL * r * r);
   f.Z = bp.take<T>(nL * r * r);
-  f.t1 = bp.take<T>(nL * r * kMaxCols);
-  f.t2 = bp.take<T>(nL * r * kMaxCols);
+  f.t1 = bp.take<T>(nL * r * kSolveCols);
+  f.t2 = bp.take<T>(nL * r * kSolveCols);
 }
 
 // the object's main arena: FP64 generators, FP64 factor, matvec and refinement
@@ -306,19 +308,8 @@ double panel_flops(int rows, int kb) {
 // triangular sweep of one node: c x c triangle plus the (b-c) x c block
 double trsv_flops(int b, int c, int nrhs) { return ((double)c * c + 2.0 * (b - c) * c) * nrhs; }
 
-// vec_seg := vec_seg - V op(T) (Vᵀ vec_seg), op(T) = Tᵀ for Qᵀ and T for Q
-template <typename T>
-void apply_q(hss_s* h, Factor<T>& f, const LevelT<T>& P, T* vec, int ldv, int nc, bool transpose,
-             cudaStream_t st) {
-  const int b = P.b, r = P.r, n = P.n;
-  const long long s1 = (long long)r * kMaxCols;
-  gemm<T>(h, true, false, r, nc, b, T(1), P.V, b, (long long)b * r, vec, ldv, b, T(0), f.t1, r, s1,
-          n, st);
-  gemm<T>(h, transpose, false, r, nc, r, T(1), P.T_, r, (long long)r * r, f.t1, r, s1, T(0), f.t2,
-          r, s1, n, st);
-  gemm<T>(h, false, false, b, nc, r, T(-1), P.V, b, (long long)b * r, f.t2, r, s1, T(1), vec, ldv,
-          b, n, st);
-}
+// (I - V op(T) Vᵀ) on b x nrhs: two b x r products and one r x r
+double qapply_flops(int b, int r, int nrhs) { return (4.0 * b * r + 2.0 * r * r) * nrhs; }
 
 enum { SPLIT_D = 1, SPLIT_U = 2, SPLIT_E = 4, SPLIT_S = 8, SPLIT_ALL = 15 };
 cudaError_t split_generators(hss_s* h, cudaStream_t st, int which);
@@ -532,6 +523,21 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
 
 // the ULV sweeps on nc <= kSolveCols columns of x (in place), arithmetic T;
 // the root solve is FP64 in every mode
+// vec_seg := vec_seg - V op(T) (Vᵀ vec_seg), op(T) = Tᵀ for Qᵀ and T for Q, as
+// three batched GEMMs over the level (used where the level has many nodes)
+template <typename T>
+void apply_q(hss_s* h, Factor<T>& f, const LevelT<T>& P, T* vec, int ldv, int nc, bool transpose,
+             cudaStream_t st) {
+  const int b = P.b, r = P.r, n = P.n;
+  const long long s1 = (long long)r * kSolveCols;
+  gemm<T>(h, true, false, r, nc, b, T(1), P.V, b, (long long)b * r, vec, ldv, b, T(0), f.t1, r, s1,
+          n, st);
+  gemm<T>(h, transpose, false, r, nc, r, T(1), P.T_, r, (long long)r * r, f.t1, r, s1, T(0), f.t2,
+          r, s1, n, st);
+  gemm<T>(h, false, false, b, nc, r, T(-1), P.V, b, (long long)b * r, f.t2, r, s1, T(1), vec, ldv,
+          b, n, st);
+}
+
 template <typename T>
 int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) {
   const int L = h->L, r = h->rank;
@@ -540,10 +546,17 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     LevelT<T>& Q = f.lv[l - 1];
     T* vec = (l == L) ? x : P.yv;
     const int ldv = (l == L) ? ld : P.n * P.b;
-    apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/true, st);
-    Launch k(h, HSS_K_TRSV_FWD, trsv_flops(P.b, P.c, nc) * P.n, st, sizeof(T) == 4);
-    HSS_TRY(launch_trsv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                       Q.n * Q.b, r, P.n, st));
+    // Qᵀ then the forward triangular sweep: fused in one launch where the level
+    // is narrow (the launches, not the flops, set its time), else three
+    // batched GEMMs and the sweep
+    const bool fused = P.n <= kFuseNodes;
+    if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/true, st);
+    Launch k(h, HSS_K_TRSV_FWD,
+             (trsv_flops(P.b, P.c, nc) + (fused ? qapply_flops(P.b, r, nc) : 0.0)) * P.n, st,
+             sizeof(T) == 4);
+    HSS_TRY(launch_ulv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                              Q.n * Q.b, r, fused ? P.V : nullptr, (long long)P.b * r, P.T_,
+                              (long long)r * r, r, P.n, st));
   }
   const int b0 = 2 * r;
   double* rootA;
@@ -580,12 +593,17 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     LevelT<T>& Q = f.lv[l - 1];
     T* vec = (l == L) ? x : P.yv;
     const int ldv = (l == L) ? ld : P.n * P.b;
+    // the backward triangular sweep then Q (fused where the level is narrow)
+    const bool fused = P.n <= kFuseNodes;
     {
-      Launch k(h, HSS_K_TRSV_BWD, trsv_flops(P.b, P.c, nc) * P.n, st, sizeof(T) == 4);
-      HSS_TRY(launch_trsv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                         Q.n * Q.b, r, P.n, st));
+      Launch k(h, HSS_K_TRSV_BWD,
+               (trsv_flops(P.b, P.c, nc) + (fused ? qapply_flops(P.b, r, nc) : 0.0)) * P.n, st,
+               sizeof(T) == 4);
+      HSS_TRY(launch_ulv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
+                                Q.n * Q.b, r, fused ? P.V : nullptr, (long long)P.b * r, P.T_,
+                                (long long)r * r, r, P.n, st));
     }
-    apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/false, st);
+    if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/false, st);
   }
   return check_launch();
 }

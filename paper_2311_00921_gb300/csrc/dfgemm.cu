@@ -7,9 +7,10 @@
 //    (exact, by one FMA), plus the low part t = ah bl + al bh + e, rounded in
 //    FP32 (relative size 2^-24 of p, so its rounding costs ~2^-48 of p); al bl
 //    (~2^-48 of p) is dropped;
-//  * accumulation into (S, C): two-sum s + err = S + p (Knuth), c = C + err + t
-//    (rounded), then the fast two-sum renormalisation S = fl(s + c),
-//    C = c - (S - s), which keeps |C| <= ulp(S) / 2 for the next term.
+//  * accumulation into (S, C): two-sum s + err = S + p (Knuth) into S, and
+//    C += err + t (rounded); every 4 terms the fast two-sum renormalisation
+//    S = fl(S + C), C = C - (S_new - S_old) brings |C| back to <= ulp(S) / 2,
+//    so C's own rounding stays near 2^-48 of S per step.
 // Every operation is written with the _rn intrinsics, which the compiler never
 // contracts into FMAs or reassociates: the transformations rely on the exact
 // rounding of each step.
@@ -23,6 +24,8 @@ namespace {
 constexpr int DT = 128;   // threads: 32 lanes along rows x 4 warps along columns
 constexpr int DK = 16;    // k per shared-memory stage
 
+// (S, C) += a b without renormalisation: S takes the two-sum of the leading
+// product, C the rounding errors and the low-order products
 HSS_DEVINL void df_mac(float& S, float& C, float ah, float al, float bh, float bl) {
   const float p = __fmul_rn(ah, bh);
   const float e = __fmaf_rn(ah, bh, -p);
@@ -30,9 +33,15 @@ HSS_DEVINL void df_mac(float& S, float& C, float ah, float al, float bh, float b
   const float s = __fadd_rn(S, p);
   const float v = __fsub_rn(s, S);
   const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, v)), __fsub_rn(p, v));
-  const float c = __fadd_rn(C, __fadd_rn(err, t));
-  S = __fadd_rn(s, c);
-  C = __fsub_rn(c, __fsub_rn(S, s));
+  C = __fadd_rn(C, __fadd_rn(err, t));
+  S = s;
+}
+
+// fast two-sum renormalisation: |C| <= ulp(S) / 2 afterwards
+HSS_DEVINL void df_norm(float& S, float& C) {
+  const float s = __fadd_rn(S, C);
+  C = __fsub_rn(C, __fsub_rn(s, S));
+  S = s;
 }
 
 // (S, C) += (h, l)
@@ -153,6 +162,12 @@ df_gemm_kernel(int m, int n, int k, const float* __restrict__ Ah, const float* _
       for (int p = 0; p < RPT; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) df_mac(S[p][q], C[p][q], ah[p], al[p], bh[q], bl[q]);
+      if ((kk & 3) == 3) {   // every 4 terms
+#pragma unroll
+        for (int p = 0; p < RPT; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) df_norm(S[p][q], C[p][q]);
+      }
     }
     __syncthreads();
   }
@@ -167,6 +182,7 @@ df_gemm_kernel(int m, int n, int k, const float* __restrict__ Ah, const float* _
       if (gi >= m) continue;
       const long long off = bz * sC + gi + (long long)gj * ldc;
       float s = S[p][q], c = C[p][q];
+      df_norm(s, c);
       if (ACC) df_add(s, c, Ch[off], Cl[off]);
       if (OUT64) {
         C64[bz * sC + gi + (long long)gj * ldc64] = ((double)s + (double)c) * unscale;

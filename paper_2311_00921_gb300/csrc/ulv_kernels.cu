@@ -649,35 +649,186 @@ HSS_DEVINL void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// rows k0 .. b-1 of columns k0 .. k0+kb-1 of M into Lp (pitch P), one commit group
+// 16 consecutive values from 16-byte aligned shared memory, in 128-bit loads
+HSS_DEVINL void load16(const float* p, float (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 f = reinterpret_cast<const float4*>(p)[q];
+    v[4 * q] = f.x;
+    v[4 * q + 1] = f.y;
+    v[4 * q + 2] = f.z;
+    v[4 * q + 3] = f.w;
+  }
+}
+HSS_DEVINL void load16(const double* p, double (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double2 f = reinterpret_cast<const double2*>(p)[q];
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+
+// rows [row0, row0+nrows) of columns [col0, col0+ncols) of src (leading
+// dimension ld) into dst[(i - row0) + (c - col0) * P], one commit group
+template <typename T>
+HSS_DEVINL void stage_block(const T* src, int ld, int row0, int nrows, int col0, int ncols, T* dst,
+                            int P) {
+  const T* s0 = src + row0 + (long long)col0 * ld;
+  for (int cc = 0; cc < ncols; ++cc)
+    for (int ii = threadIdx.x; ii < nrows; ii += NT)
+      cp_async_elem(dst + ii + cc * P, s0 + ii + (long long)cc * ld);
+  cp_async_commit();
+}
+
+// rows k0 .. b-1 of columns k0 .. k0+kb-1 of M into Lp (pitch P)
 template <typename T>
 HSS_DEVINL void stage_panel(const T* M, int ldm, int k0, int kb, int b, T* Lp, int P) {
-  const int n1 = b - k0;
-  for (int e = threadIdx.x; e < n1 * kb; e += NT) {
-    const int ii = e % n1, t = e / n1;
-    cp_async_elem(Lp + ii + t * P, M + (k0 + ii) + (long long)(k0 + t) * ldm);
+  stage_block(M, ldm, k0, b - k0, k0, kb, Lp, P);
+}
+
+// Padded pitch of the partial-sum scratch (conflict-free scalar stores)
+constexpr int ZP = 17;
+
+// y (b x nrhs in shared memory, ld b) := (I - V op(T) Vᵀ) y, op(T) = Tᵀ for the
+// forward sweep (Qᵀ y) and T for the backward one (Q y).  V (b x r) and T
+// (r x r) of the node stream through the panel buffers in CB-column slabs.  yr
+// holds y row by row (pitch 16, zero past nrhs; filled here when fill is set),
+// t1, t2 hold r x 16 row by row, zp NT x ZP partial sums.  The products read a
+// row of 16 right-hand sides with 128-bit loads that every lane shares, so
+// each FMA costs about a third of a shared load.  Called by every thread with
+// y visible; returns with no copy in flight.
+template <typename T>
+HSS_DEVINL void q_apply(T* y, T* yr, bool fill, int b, int nrhs, const T* V, const T* Tm, int r,
+                        bool transpose, T* Lbuf, int P, int CB, int NBUF, T* zp, T* t1, T* t2) {
+  const int tid = threadIdx.x;
+  const int ns = (r + CB - 1) / CB;
+  auto buf = [&](int sl) { return Lbuf + (size_t)(NBUF == 2 ? (sl & 1) : 0) * P * CB; };
+  if (fill) {
+    for (int e = tid; e < b * 16; e += NT) {
+      const int i = e / 16, j = e % 16;
+      yr[e] = j < nrhs ? y[i + j * b] : T(0);
+    }
   }
-  cp_async_commit();
+  __syncthreads();
+  const int q = tid % CB, g = tid / CB, NG = NT / CB;   // slab column, row group
+  T acc2[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc2[j] = T(0);
+  // (0) t1 = Vᵀ y and (2) y -= V t2 stream V; (1) t2 = op(T) t1 streams T
+  for (int phase = 0; phase < 3; ++phase) {
+    const T* src = phase == 1 ? Tm : V;
+    const int rows = phase == 1 ? r : b;
+    stage_block(src, rows, 0, rows, 0, min(CB, r), buf(0), P);
+    for (int sl = 0; sl < ns; ++sl) {
+      const int q0 = sl * CB, qn = min(CB, r - q0);
+      const bool next = sl + 1 < ns;
+      if (NBUF == 2 && next) {
+        stage_block(src, rows, 0, rows, q0 + CB, min(CB, r - q0 - CB), buf(sl + 1), P);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const T* S = buf(sl);
+      if (phase == 0 || (phase == 1 && transpose)) {
+        // out row (q0 + q) = Σ_i S(i, q) in row i: row groups g, then summed
+        const T* in = phase == 0 ? yr : t1;
+        T* out = phase == 0 ? t1 : t2;
+        T a[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) a[j] = T(0);
+        if (q < qn) {
+          for (int i = g; i < rows; i += NG) {
+            const T sv = S[i + q * P];
+            T v[16];
+            load16(in + i * 16, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = fma(sv, v[j], a[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) zp[(g * CB + q) * ZP + j] = a[j];
+        __syncthreads();
+        for (int e = tid; e < qn * 16; e += NT) {
+          const int qq = e / 16, j = e % 16;
+          T sum = T(0);
+          for (int gg = 0; gg < NG; ++gg) sum += zp[(gg * CB + qq) * ZP + j];
+          out[(q0 + qq) * 16 + j] = sum;
+        }
+      } else if (phase == 1) {
+        // t2 row (tid) += Σ_{p in slab} T(tid, p) t1 row p
+        if (tid < r) {
+          for (int pp = 0; pp < qn; ++pp) {
+            const T tv = S[tid + pp * P];
+            T v[16];
+            load16(t1 + (q0 + pp) * 16, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc2[j] = fma(tv, v[j], acc2[j]);
+          }
+        }
+      } else {
+        // y(i, :) -= Σ_{q in slab} V(i, q) t2 row q
+        for (int i = tid; i < b; i += NT) {
+          T a[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) a[j] = T(0);
+          for (int qq = 0; qq < qn; ++qq) {
+            const T sv = S[i + qq * P];
+            T v[16];
+            load16(t2 + (q0 + qq) * 16, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = fma(sv, v[j], a[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j < nrhs) y[i + j * b] -= a[j];
+        }
+      }
+      __syncthreads();
+      if (NBUF == 1 && next)
+        stage_block(src, rows, 0, rows, q0 + CB, min(CB, r - q0 - CB), buf(sl + 1), P);
+    }
+    if (phase == 1 && !transpose && tid < r) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) t2[tid * 16 + j] = acc2[j];
+    }
+    __syncthreads();
+  }
 }
 
 // forward: y (b x nrhs, smem) := [L^RR⁻¹ y^R ; y^S - L^SR L^RR⁻¹ y^R]
 template <typename T>
 __global__ void __launch_bounds__(NT)
 trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
-                long long sX, int nrhs, T* Par, int ldpar, long long sPar, int CB, int NBUF) {
+                long long sX, int nrhs, T* Par, int ldpar, long long sPar, const T* Vb,
+                long long sV, const T* Tb, long long sT, int r, int CB, int NBUF) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) T zt[NB * 16];
   T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs, ld = b
   const int P = b | 1;
-  T* Lbuf = y + (size_t)b * nrhs;          // NBUF panels of P x CB
+  // Q application (Vb given): y row by row, partial sums, t1 and t2 (r x 16)
+  const size_t qsz = Vb ? (size_t)b * 16 + (size_t)NT * ZP + (size_t)32 * r : 0;
+  T* yr = y + (((size_t)b * nrhs + 15) & ~size_t(15));
+  T* zpq = yr + (size_t)b * 16;
+  T* t1 = zpq + (size_t)NT * ZP;
+  T* t2 = t1 + (size_t)16 * r;
+  T* Lbuf = yr + qsz;                      // NBUF panels of P x CB
   const int node = blockIdx.x;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
   const int nblk = (c + CB - 1) / CB;
-  if (nblk > 0) stage_panel(M, ldm, 0, min(CB, c), b, Lbuf, P);
+  if (!Vb && nblk > 0) stage_panel(M, ldm, 0, min(CB, c), b, Lbuf, P);
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     y[i + j * b] = x[i + (long long)j * ldx];
+  }
+  if (Vb) {   // y := Qᵀ y, then the first panel
+    __syncthreads();
+    q_apply(y, yr, true, b, nrhs, Vb + (long long)node * sV, Tb + (long long)node * sT, r, true,
+            Lbuf, P, CB, NBUF, zpq, t1, t2);
+    if (nblk > 0) stage_panel(M, ldm, 0, min(CB, c), b, Lbuf, P);
   }
   for (int bi = 0; bi < nblk; ++bi) {
     const int k0 = bi * CB;
@@ -713,6 +864,12 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       }
     }
     __syncthreads();
+    // the solved block transposed (zt[t][j], zero past nrhs) for vector loads
+    for (int e = tid; e < NB * 16; e += NT) {
+      const int t = e / 16, j = e % 16;
+      zt[e] = (t < kb && j < nrhs) ? y[(k0 + t) + j * b] : T(0);
+    }
+    __syncthreads();
     // every row below the block (the S rows included: L^SR lives there)
     for (int i = k0 + kb + tid; i < b; i += NT) {
       const int ii = i - k0;
@@ -723,9 +880,10 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       for (int t = 0; t < NB; ++t) {
         if (t < kb) {
           const T l = L[ii + t * P];
+          T zv[16];
+          load16(zt + t * 16, zv);
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (j < nrhs) acc[j] = fma(l, y[(k0 + t) + j * b], acc[j]);
+          for (int j = 0; j < 16; ++j) acc[j] = fma(l, zv[j], acc[j]);
         }
       }
 #pragma unroll
@@ -755,12 +913,17 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
 template <typename T>
 __global__ void __launch_bounds__(NT)
 trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
-                long long sX, int nrhs, const T* Par, int ldpar, long long sPar, int CB,
-                int NBUF) {
+                long long sX, int nrhs, const T* Par, int ldpar, long long sPar, const T* Vb,
+                long long sV, const T* Tb, long long sT, int r, int CB, int NBUF) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs
   const int P = b | 1;
-  T* Lbuf = y + (size_t)b * nrhs;
+  // b x 16 row-major shadow of the solved rows (16-byte aligned for vector loads)
+  T* xt = y + (((size_t)b * nrhs + 15) & ~size_t(15));
+  T* zp = xt + (size_t)b * 16;             // NT x ZP partial sums
+  T* t1 = zp + (size_t)NT * ZP;
+  T* t2 = t1 + (size_t)16 * (Vb ? r : 0);
+  T* Lbuf = t2 + (size_t)16 * (Vb ? r : 0);
   const int node = blockIdx.x;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
@@ -780,6 +943,12 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       v = x[i + (long long)j * ldx];
     y[i + j * b] = v;
   }
+  __syncthreads();
+  // rows c .. b-1 (x^S) are final from the start
+  for (int e = tid; e < (b - c) * 16; e += NT) {
+    const int i = c + e / 16, j = e % 16;
+    xt[i * 16 + j] = j < nrhs ? y[i + j * b] : T(0);
+  }
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int k0 = bi * CB;
     const int kb = min(CB, c - k0);
@@ -792,19 +961,34 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       cp_async_wait<0>();
     }
     __syncthreads();
-    // z_t -= Σ_{i >= k0+kb} L(i, t) x_i: thread (t = lane, j = warp, warp + nw)
-    // runs two dependent chains down the rows
-    if (lane < kb) {
-      const int t = lane;
-      const int j0 = wid, j1 = wid + nw;
-      T a0 = T(0), a1 = T(0);
-      for (int i = k0 + kb; i < b; ++i) {
-        const T l = L[(i - k0) + t * P];
-        if (j0 < nrhs) a0 = fma(l, y[i + j0 * b], a0);
-        if (j1 < nrhs) a1 = fma(l, y[i + j1 * b], a1);
+    // z_t -= Σ_{i >= k0+kb} L(i, t) x_i: thread (t = lane, rows i ≡ warp mod nw)
+    // accumulates every right-hand side from the row-major shadow, then the
+    // warps' partial sums are added
+    {
+      T acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = T(0);
+      if (lane < kb) {
+        for (int i = k0 + kb + wid; i < b; i += nw) {
+          const T l = L[(i - k0) + lane * P];
+          T xv[16];
+          load16(xt + i * 16, xv);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = fma(l, xv[j], acc[j]);
+        }
       }
-      if (j0 < nrhs) y[(k0 + t) + j0 * b] -= a0;
-      if (j1 < nrhs) y[(k0 + t) + j1 * b] -= a1;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) zp[(wid * NB + lane) * ZP + j] = acc[j];
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * 16; e += NT) {
+      const int t = e / 16, j = e % 16;
+      if (j < nrhs) {
+        T sum = T(0);
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) sum += zp[(w * NB + t) * ZP + j];
+        y[(k0 + t) + j * b] -= sum;
+      }
     }
     __syncthreads();
     // diagonal block, transposed back substitution; lane i keeps column i of
@@ -829,9 +1013,19 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
       }
     }
     __syncthreads();
+    for (int e = tid; e < kb * 16; e += NT) {   // the block's rows are final now
+      const int i = k0 + e / 16, j = e % 16;
+      xt[i * 16 + j] = j < nrhs ? y[i + j * b] : T(0);
+    }
     if (NBUF == 1 && next) stage_panel(M, ldm, k0 - CB, CB, b, Lbuf, P);
   }
   cp_async_wait<0>();
+  if (Vb) {   // y := Q y
+    __syncthreads();
+    q_apply(y, xt, false, b, nrhs, Vb + (long long)node * sV, Tb + (long long)node * sT, r, false,
+            Lbuf, P, CB, NBUF, zp, t1, t2);
+  }
+  __syncthreads();
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     x[i + (long long)j * ldx] = y[i + j * b];
@@ -961,52 +1155,78 @@ cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T
   return cudaGetLastError();
 }
 
-// shared memory of a sweep: the node vector plus NBUF staged panels of P x CB
+// shared memory of a sweep: the node vector, the Q application's two r x 16
+// buffers, and NBUF staged panels of P x CB
 template <typename T>
-size_t trsv_smem(int b, int nrhs, int CB, int NBUF) {
-  return ((size_t)b * nrhs + (size_t)NBUF * (b | 1) * CB) * sizeof(T);
+size_t trsv_smem(int b, int nrhs, int r, int CB, int NBUF, bool bwd) {
+  // the node vector (padded to 16 elements); the row-major shadow and partial
+  // sums (backward sweep, or any Q application); t1, t2; the panels
+  const size_t vec = ((size_t)b * nrhs + 15) & ~size_t(15);
+  const size_t rowmajor = (bwd || r > 0) ? (size_t)b * 16 + (size_t)NT * ZP : 0;
+  return (vec + rowmajor + (size_t)32 * r + (size_t)NBUF * (b | 1) * CB) * sizeof(T);
 }
 
 // the largest staging the device allows: two 32-column panels, else one, else
 // 16- and 8-column panels
 template <typename T, typename K>
-cudaError_t trsv_config(K kernel, int b, int nrhs, int* CB, int* NBUF, size_t* sm) {
-  const int cbs[4] = {32, 32, 16, 8}, bufs[4] = {2, 1, 1, 1};
-  for (int q = 0; q < 4; ++q) {
+cudaError_t trsv_config(K kernel, int b, int nrhs, int r, bool bwd, int* CB, int* NBUF,
+                        size_t* sm) {
+  const int cbs[5] = {32, 32, 16, 16, 8}, bufs[5] = {2, 1, 2, 1, 1};
+  for (int q = 0; q < 5; ++q) {
     *CB = cbs[q];
     *NBUF = bufs[q];
-    *sm = trsv_smem<T>(b, nrhs, *CB, *NBUF);
+    *sm = trsv_smem<T>(b, nrhs, r, *CB, *NBUF, bwd);
     if (smem_opt_in(kernel, *sm)) return cudaSuccess;
   }
   return cudaErrorInvalidConfiguration;
 }
 
 template <typename T>
+cudaError_t launch_ulv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
+                           long long sX, int nrhs, T* Par, int ldpar, long long sPar, const T* V,
+                           long long sV, const T* Tm, long long sT, int r, int nodes,
+                           cudaStream_t st) {
+  if (nrhs > 16 || (V && (r < 1 || r > NT || r > b))) return cudaErrorInvalidValue;
+  int CB, NBUF;
+  size_t sm;
+  cudaError_t e = trsv_config<T>(trsv_fwd_kernel<T>, b, nrhs, V ? r : 0, false, &CB, &NBUF,
+                                 &sm);
+  if (e != cudaSuccess) return e;
+  trsv_fwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, V,
+                                            sV, Tm, sT, V ? r : 0, CB, NBUF);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ulv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
+                           long long sX, int nrhs, const T* Par, int ldpar, long long sPar,
+                           const T* V, long long sV, const T* Tm, long long sT, int r, int nodes,
+                           cudaStream_t st) {
+  if (nrhs > 16 || (V && (r < 1 || r > NT || r > b))) return cudaErrorInvalidValue;
+  int CB, NBUF;
+  size_t sm;
+  cudaError_t e = trsv_config<T>(trsv_bwd_kernel<T>, b, nrhs, V ? r : 0, true, &CB, &NBUF,
+                                 &sm);
+  if (e != cudaSuccess) return e;
+  trsv_bwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, V,
+                                            sV, Tm, sT, V ? r : 0, CB, NBUF);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                             long long sX, int nrhs, T* Par, int ldpar, long long sPar, int nodes,
                             cudaStream_t st) {
-  if (nrhs > 16) return cudaErrorInvalidValue;
-  int CB, NBUF;
-  size_t sm;
-  cudaError_t e = trsv_config<T>(trsv_fwd_kernel<T>, b, nrhs, &CB, &NBUF, &sm);
-  if (e != cudaSuccess) return e;
-  trsv_fwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar,
-                                            CB, NBUF);
-  return cudaGetLastError();
+  return launch_ulv_fwd<T>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, nullptr, 0,
+                           nullptr, 0, 0, nodes, st);
 }
 
 template <typename T>
 cudaError_t launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                             long long sX, int nrhs, const T* Par, int ldpar, long long sPar,
                             int nodes, cudaStream_t st) {
-  if (nrhs > 16) return cudaErrorInvalidValue;
-  int CB, NBUF;
-  size_t sm;
-  cudaError_t e = trsv_config<T>(trsv_bwd_kernel<T>, b, nrhs, &CB, &NBUF, &sm);
-  if (e != cudaSuccess) return e;
-  trsv_bwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar,
-                                            CB, NBUF);
-  return cudaGetLastError();
+  return launch_ulv_bwd<T>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, nullptr, 0,
+                           nullptr, 0, 0, nodes, st);
 }
 
 void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t st) {
@@ -1022,6 +1242,12 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
                                           int, T*, int, long long, int, cudaStream_t);            \
   template cudaError_t launch_trsv_bwd<T>(const T*, int, long long, int, int, T*, int, long long, \
                                           int, const T*, int, long long, int, cudaStream_t);      \
+  template cudaError_t launch_ulv_fwd<T>(const T*, int, long long, int, int, T*, int, long long,  \
+                                         int, T*, int, long long, const T*, long long, const T*,  \
+                                         long long, int, int, cudaStream_t);                      \
+  template cudaError_t launch_ulv_bwd<T>(const T*, int, long long, int, int, T*, int, long long,  \
+                                         int, const T*, int, long long, const T*, long long,      \
+                                         const T*, long long, int, int, cudaStream_t);            \
   template size_t ql_smem<T>(int, int);                                                          \
   template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int, int,\
                                             int*, int, bool, cudaStream_t);                       \
