@@ -7,6 +7,8 @@
 // CTAs to cover all 152 SMs.  Tall-skinny products (n <= 32 columns, the
 // right-hand-side blocks of the solve and matvec) use a separate kernel whose
 // warps own whole columns, so that no warp issues DFMAs on padding.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace {
@@ -294,6 +296,123 @@ gemm_n16_small_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int
   }
 }
 
+// FP32 128 x 128 tile for wide products (the diagonal product of the FP32
+// factor): 256 threads with an 8 x 8 micro-tile each, split into four 4 x 4
+// quadrants (rows 4 tx and 64 + 4 tx, columns 4 ty and 64 + 4 ty) so that every
+// operand fragment is one 128-bit shared load: 4 loads per 64 FMAs.  The next
+// K slab is fetched into registers while the current one is multiplied, into
+// the other of two shared-memory buffers (one barrier per slab).
+constexpr int SBM = 128, SBK8 = 8;
+
+template <bool TA, bool TB, bool BETA>
+__global__ void __launch_bounds__(256)
+sgemm128_kernel(int m, int n, int k, float alpha, const float* __restrict__ A, int lda,
+                long long sA, const float* __restrict__ B, int ldb, long long sB, float beta,
+                float* C, int ldc, long long sC) {
+  __shared__ __align__(16) float As[2][SBK8][SBM];
+  __shared__ __align__(16) float Bs[2][SBK8][SBM];
+  const long long bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int i0 = blockIdx.x * SBM, j0 = blockIdx.y * SBM;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // slab element e = tid + 256 q (q < 4) of the 128 x 8 A slab and the 8 x 128 B slab
+  float ra[4], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int i, kk;
+      if (!TA) { i = e % SBM; kk = e / SBM; } else { kk = e % SBK8; i = e / SBK8; }
+      const int gi = i0 + i, gk = k0 + kk;
+      ra[q] = (gi < m && gk < k) ? (TA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda])
+                                 : 0.f;
+      int j, kb;
+      if (!TB) { kb = e % SBK8; j = e / SBK8; } else { j = e % SBM; kb = e / SBM; }
+      const int gj = j0 + j, gkb = k0 + kb;
+      rb[q] = (gj < n && gkb < k) ? (TB ? B[gj + (long long)gkb * ldb] : B[gkb + (long long)gj * ldb])
+                                  : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int i, kk;
+      if (!TA) { i = e % SBM; kk = e / SBM; } else { kk = e % SBK8; i = e / SBK8; }
+      As[buf][kk][i] = ra[q];
+      int j, kb;
+      if (!TB) { kb = e % SBK8; j = e / SBK8; } else { j = e % SBM; kb = e / SBM; }
+      Bs[buf][kb][j] = rb[q];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  fetch(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < k; k0 += SBK8) {
+    const bool more = k0 + SBK8 < k;
+    if (more) fetch(k0 + SBK8);
+#pragma unroll
+    for (int kk = 0; kk < SBK8; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * tx]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + 4 * tx]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * ty]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + 4 * ty]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int gj = j0 + (q < 4 ? 4 * ty + q : 64 + 4 * ty + q - 4);
+    if (gj >= n) continue;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const int gi = i0 + (p < 4 ? 4 * tx + p : 64 + 4 * tx + p - 4);
+      if (gi >= m) continue;
+      float* c = C + gi + (long long)gj * ldc;
+      *c = BETA ? fmaf(alpha, acc[p][q], beta * *c) : alpha * acc[p][q];
+    }
+  }
+}
+
+// the FP32 wide tile where its 128 x 128 tiles still fill the GPU twice over
+template <typename T, bool TA, bool TB>
+bool launch_sgemm128(int m, int n, int k, T alpha, const T* A, int lda, long long sA, const T* B,
+                     int ldb, long long sB, T beta, T* C, int ldc, long long sC, int batch,
+                     cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    const long long tiles = (long long)((m + SBM - 1) / SBM) * ((n + SBM - 1) / SBM) * batch;
+    if (n < 64 || m < 64 || tiles < 2 * 152) return false;
+    dim3 g((m + SBM - 1) / SBM, (n + SBM - 1) / SBM, batch);
+    if (beta != 0.f)
+      sgemm128_kernel<TA, TB, true><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
+                                                       beta, C, ldc, sC);
+    else
+      sgemm128_kernel<TA, TB, false><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
+                                                        beta, C, ldc, sC);
+    return true;
+  } else {
+    return false;
+  }
+}
+
 template <typename T, bool TA, bool TB>
 void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA, const T* B,
                  int ldb, long long sB, T beta, T* C, int ldc, long long sC, int batch,
@@ -329,6 +448,9 @@ void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA
                                                             sB, beta, C, ldc, sC);
     return;
   }
+  if (launch_sgemm128<T, TA, TB>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+                                 st))
+    return;
   dim3 g((m + BM - 1) / BM, (n + BN - 1) / BN, batch);
   if (useb)
     gemm_tile_kernel<T, TA, TB, true><<<g, NT, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
