@@ -176,8 +176,9 @@ KERNEL_SOURCES = {"tc_gemm": "tc_gemm_kernel", "tc_syr2k": "tc_gemm_kernel",
                   "gemm_skinny": "gemm_n16_kernel", "trsv_fwd": "trsv_fwd_kernel",
                   "trsv_bwd": "trsv_bwd_kernel", "other": "logdet_reduce_kernel",
                   "pair_gemm": "df_gemm_kernel"}
-# pair-of-FP32 arithmetic: 15 FP32 instructions per multiply-add (2 flops)
-PAIR_OPS_PER_FLOP = 7.5
+# pair-of-FP32 arithmetic: 12 FP32 instructions per multiply-add (2 flops) plus a
+# 3-instruction renormalisation every 4 terms
+PAIR_OPS_PER_FLOP = 12.75 / 2
 
 
 def workload(args):
@@ -276,7 +277,7 @@ def measured_peaks(torch):
 
 
 PEAK_SOURCE = {"pair32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured in this run, "
-                         "/ 7.5: the pair arithmetic spends 15 FP32 instructions per "
+                         "/ 6.375: the pair arithmetic spends 12.75 FP32 instructions per "
                          "multiply-add",
                "f64": "cuBLAS DGEMM 8192^3 (FP64 pipe) measured in this run",
                "f32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured in this run",
