@@ -114,3 +114,25 @@ def test_invalid_residual_option():
     opt = hss.Options(hss.PRECISIONS["fp32"], 30, 1e-12, 7, 0)
     rc = hss.load().hss_factorize(dev._h, ctypes.byref(opt), None)
     assert rc == -1
+
+
+def test_wide_levels_mixed_against_fp64():
+    """128 leaves of 512 (N = 65,536): launches wide enough for the FP32 128 x 128
+    GEMM tile, the 128-row pair-GEMM tiles and the batched-GEMM Q application of
+    the solve.  The mixed solution (pair residual) has a true FP64 residual
+    <= 1e-12 and agrees with the FP64 factor's solution to 1e-10."""
+    h = I.random_hss(7, 512, 64, seed=27, orthonormal=False, fast_bound=True)
+    dev = hss.HSS(h)
+    b = I.rhs(h.n, 3, 10)
+    dev.factorize("fp64")
+    x64 = dev.solve(hss.colmajor(b)).cpu().numpy()
+    dev.factorize("fp32", residual="pair32")
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    info = dev.last_info()
+    assert info["code"] == 0 and info["ir_resid"] <= 1e-12, info
+    res = b - O.matvec(h, x)
+    assert (np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)).max() <= 1e-12
+    err = np.linalg.norm(x - x64, axis=0) / np.linalg.norm(x64, axis=0)
+    assert err.max() <= 1e-10, err
+    res64 = b - O.matvec(h, x64)
+    assert (np.linalg.norm(res64, axis=0) / np.linalg.norm(b, axis=0)).max() <= 1e-12
