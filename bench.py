@@ -344,6 +344,29 @@ def roofline_of(tr, peaks, steps, prec_mode="fp64"):
                                   for k, v in sorted(tr.items())}}
 
 
+def replica_workload(base, rank):
+    """Rank `rank`'s matrix under --gpus N: the same workload shape with its own
+    seed (the ranks run independent replicas; there is no data exchange)."""
+    import dataclasses
+    return dataclasses.replace(base, seed=base.seed + 10 * rank)
+
+
+def max_over_ranks(value, dist, device):
+    """The largest `value` over all ranks (the slowest rank's step time); the
+    value itself when there is no process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(world, flops_per_step, ms_per_step):
+    """Whole-job throughput: every rank's step of flops_per_step in ms_per_step."""
+    return world * flops_per_step / (ms_per_step / 1e3) / 1e12
+
+
 def run_ours(args):
     import torch
     from paper_2311_00921_gb300 import hss, inputs as I
@@ -357,9 +380,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    base = workload(args)
-    import dataclasses
-    w = dataclasses.replace(base, seed=base.seed + 10 * rank)
+    w = replica_workload(workload(args), rank)
     h = I.cached_build(w, os.environ.get("HSS_INPUT_CACHE"))
     dev = hss.HSS(h)
     b_host = I.rhs(w.n, w.nrhs, w.seed + 1)
@@ -377,13 +398,9 @@ def run_ours(args):
     if dist:
         dist.barrier()
     head = timed_steps(torch, dev, b, x, prec, args.steps, ClockSampler(local), resid)
-    ms = head["ms"]
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(head["ms"], dist, "cuda")
     ms_step = ms / args.steps
-    value = world * fl_step / (ms_step / 1e3) / 1e12
+    value = job_tflops(world, fl_step, ms_step)
     # correctness of the timed result: FP64 residual through the HSS matvec
     r = b - dev.matvec(x)
     rel = (torch.linalg.vector_norm(r, dim=0) / torch.linalg.vector_norm(b, dim=0)).max().item()
@@ -576,12 +593,8 @@ def run_e2e(args, h, w, b_host, prec, fl_step, world, dist):
         xh.copy_(xd, non_blocking=True)
         torch.cuda.synchronize()
         lib.hss_destroy(out)
-    dt = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-    return {"value": world * fl_step * steps / dt / 1e12, "unit": "TFLOP/s",
+    dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    return {"value": job_tflops(world, fl_step, 1e3 * dt / steps), "unit": "TFLOP/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": 1e3 * dt / steps, "steps": steps,
             "includes": "hss_create from pinned host (generators H2D), factorize, b H2D, "
