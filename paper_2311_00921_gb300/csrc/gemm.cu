@@ -6,7 +6,11 @@
 // thread against 8 shared-memory loads, and the only other goal is enough
 // CTAs to cover all 152 SMs.  Tall-skinny products (n <= 32 columns, the
 // right-hand-side blocks of the solve and matvec) use a separate kernel whose
-// warps own whole columns, so that no warp issues DFMAs on padding.
+// warps own whole columns, so that no warp issues DFMAs on padding.  The FP32
+// factor's wide products get their own 128 x 128 tile (sgemm128_kernel), since
+// on the FP32 pipe the 4x4 micro-tile's shared-memory loads, not the FMAs, set
+// the rate.  syr2k_lower_kernel also serves as the SYRK of the blocked partial
+// Cholesky (template flag SYRK).
 #include <type_traits>
 
 #include "common.cuh"

@@ -5,17 +5,21 @@
 //                         column-reversed copy (LAPACK dlarfg signs), giving
 //                         Q = I - V T Vᵀ = [Q^R Q^S] with the redundant part first,
 //                         and L_B = Q^Sᵀ B (r x r, lower triangular).
-//  * pchol_kernel      -- partial Cholesky, Eq. partial-Cholesky (Alg. 2 line 3):
-//                         right-looking blocked Cholesky of the first c = b - r
-//                         columns of Â (lower triangle).  It leaves L^RR, L^SR
-//                         and the Schur complement Â^SS; its epilogue is the merge
-//                         (Alg. 2 line 4): Â^SS is written straight into the
-//                         parent's diagonal block (a gather, no separate pass).
-//                         With c = b and no parent it is the root Cholesky (line 6).
+//  * chol_panel_kernel -- one 32-column panel of the partial Cholesky, Eq.
+//                         partial-Cholesky (Alg. 2 line 3), for every node of a
+//                         level: POTRF of the diagonal block and TRSM of the rows
+//                         below it; the trailing SYRK is a level-wide launch
+//                         (gemm.cu).  With c = b it is the panel of the root
+//                         Cholesky (line 6).
+//  * scatter_ss_kernel -- the merge (Alg. 2 line 4): Â^SS of each node into its
+//                         parent's diagonal block.
+//  * pchol_kernel      -- the whole partial Cholesky of a node in one CTA, with
+//                         the merge as its epilogue (the batched forest path).
 //  * trsv_fwd_kernel /
-//    trsv_bwd_kernel   -- the triangular parts of the ULV solve (Sec. 3.2): forward
-//                         z^R = L^RR⁻¹ y^R, y^S -= L^SR z^R (pushed to the parent's
-//                         vector), and backward x^R = L^RR⁻ᵀ (z^R - L^SRᵀ x^S).
+//    trsv_bwd_kernel   -- one level of the ULV solve (Sec. 3.2): forward
+//                         y := Qᵀ y (optionally), z^R = L^RR⁻¹ y^R, y^S -= L^SR z^R
+//                         (pushed to the parent's vector); backward
+//                         x^R = L^RR⁻ᵀ (z^R - L^SRᵀ x^S), then x := Q x (optionally).
 //  * logdet_reduce_kernel -- 2 Σ log diag over all nodes, fixed summation order.
 #include <math.h>
 
@@ -49,13 +53,6 @@ HSS_DEVINL T warp_transpose_reduce(T (&acc)[NV], int lane) {
     }
   }
   return acc[0];
-}
-
-// reflector jj of the panel starting at column j0, row i (unit at j0 + jj, zero above)
-template <typename T>
-HSS_DEVINL T vpan(const T* P, int b, int j0, int jj, int i) {
-  const int d = j0 + jj;
-  return i > d ? P[i + jj * b] : (i == d ? T(1) : T(0));
 }
 
 // CTA-level product O(q, c) = Σ_{i >= i0} Pt(q, i) A(i, c) for q < NBP and the
