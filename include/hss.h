@@ -75,7 +75,7 @@ typedef enum {
 
 typedef struct {
   int32_t n;      /* matrix order, = leaf * 2^levels */
-  int32_t leaf;   /* leaf block order (1 .. 768) */
+  int32_t leaf;   /* leaf block order (1 .. 768; FP64 solves: see hss_solve) */
   int32_t rank;   /* rank of every basis (1 .. min(leaf, 256)) */
   int32_t levels; /* L >= 1 */
 } hss_shape;
@@ -126,7 +126,10 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream);
  * FP64 factor the call is asynchronous.  With a mixed factor it runs FP64
  * iterative refinement (residual by the HSS matvec) and synchronizes once per
  * iteration; it returns HSS_ERR_NO_CONVERGENCE if ir_max_it is reached (x then
- * holds the last iterate).  Errors: NOT_FACTORIZED, INVALID_ARG, CUDA. */
+ * holds the last iterate).  Errors: NOT_FACTORIZED, INVALID_ARG, CUDA.
+ * Shared memory bounds one level's sweep: with an FP64 factor and 16 columns per
+ * pass (nrhs >= 16) the leaf order must be <= 617, else INVALID_ARG (fewer
+ * columns allow larger leaves; FP32 factors allow every leaf up to 768). */
 int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, void* stream);
 
 /* log det A from the factorized form (Eq. hss-ulv-final-form): twice the sum of
