@@ -123,8 +123,9 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream);
  * (apply Qᵀ, L^RR⁻¹, update and push the skeleton part to the parent), root
  * Cholesky solve, backward sweep root -> leaves.  b and x are device pointers,
  * n x nrhs column-major with leading dimension ld >= n; x may equal b.  With an
- * FP64 factor the call is asynchronous.  With a mixed factor it runs FP64
- * iterative refinement (residual by the HSS matvec) and synchronizes once per
+ * FP64 factor the call is asynchronous.  With a mixed factor it runs iterative
+ * refinement with an FP64 iterate, update and stopping test (residual by the HSS
+ * matvec in the arithmetic hss_options.residual selects) and synchronizes once per
  * iteration; it returns HSS_ERR_NO_CONVERGENCE if ir_max_it is reached (x then
  * holds the last iterate).  Errors: NOT_FACTORIZED, INVALID_ARG, CUDA.
  * Shared memory bounds one level's sweep: with an FP64 factor and 16 columns per
