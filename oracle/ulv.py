@@ -271,8 +271,6 @@ def matvec(h, x: np.ndarray) -> np.ndarray:
         for k, S in enumerate(h.S[l]):
             yh[l][2 * k + 1] += S @ xh[l][2 * k]
             yh[l][2 * k] += S.T @ xh[l][2 * k + 1]
-        if l > 1:      # pass the parents' accumulated fields down to this level
-            pass
     for l in range(1, L):
         for i in range(2 ** l):
             t = h.E[l][i] @ yh[l][i]
