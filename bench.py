@@ -5,15 +5,19 @@ Workload: the N = 262,144 HSS matrix of the Yukawa kernel exp(-d)/(d + 1e-3)
 plus 64 I on points uniform on the unit sphere (leaf 512, rank 128, 9 levels),
 16 N(0,1) right-hand sides; seeded synthetic data in place of the paper's
 grids.  One step = one factorization (Alg. 2) + one solve of all right-hand
-sides.  ``value`` is the canonical-model TFLOP/s of that step (the paper's
-dense formulation: explicit Q, QᵀDQ as 4b³ per node), with inputs resident in
-HBM; ``e2e`` is the same metric through the C ABI from pinned host buffers,
-copies included.  Under torchrun each rank factors its own independent matrix
-(different seed) -- weak scaling, no collective on the data path.
+sides.  The headline step factors in FP32 and refines to a 1e-12 relative
+residual with the residual HSS matvec, the update and the root Cholesky in
+FP64.  ``variants`` holds the same step with the pair-of-FP32 residual, the
+tensor-core TF32 / BF16 factors, and ``fp64`` the all-FP64 path.  ``value`` is
+the canonical-model TFLOP/s of the step (the paper's dense formulation:
+explicit Q, QᵀDQ as 4b³ per node), with inputs resident in HBM; ``e2e`` is the
+same metric through the C ABI from pinned host buffers, copies included.
+Under torchrun each rank factors its own independent matrix (different seed)
+-- weak scaling, no collective on the data path.
 
 ``--impl reference`` times the CPU oracle (NumPy/SciPy FP64, as it stands) on a
-bounded sample of the same workload: the subtree of one level-3 node (an HSS
-matrix of order 32,768 with the same leaf size, rank and kernel).
+bounded sample of the same workload per step: the subtree of one level-4 node
+(an HSS matrix of order 16,384 with the same leaf size, rank and kernel).
 """
 import argparse
 import hashlib
@@ -33,7 +37,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "HSS-ULV factor+solve time & TFLOP/s, N=2^18: FP64 vs mixed+IR to 1e-12 residual"
 WORKLOAD = "sphere_yukawa_256k"
-SAMPLE_LEVEL = 3        # cpu baseline: subtree of one node of this level
+SAMPLE_LEVEL = 3        # cpu baseline: subtree of one node of this level (N = 32,768)
+REFERENCE_LEVEL = 4     # --impl reference: per-step sample (N = 16,384), so that
+                        # K + W steps of the oracle end within a few minutes
 
 
 # ---------------------------------------------------------------- flop model
@@ -148,9 +154,10 @@ def measured_fp64_peak(torch):
     return 2 * 8192 ** 3 / best / 1e12
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    if the kernel source changed since those counters were taken."""
+def traffic_record(kernel, prec):
+    """DRAM bytes per launch of `kernel` in arithmetic `prec` from the committed
+    ncu summary, or None if the kernel source changed since those counters were
+    taken."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -158,7 +165,7 @@ def traffic_record(kernel):
         if line.startswith("#") or not line.strip():
             continue
         kv = dict(x.split("=", 1) for x in line.split())
-        if kv.get("kernel") != kernel:
+        if kv.get("kernel") != kernel or kv.get("prec", "f64") != prec:
             continue
         src = os.path.join(ROOT, "paper_2311_00921_gb300", "csrc", kv["src"])
         if not os.path.exists(src):
@@ -190,12 +197,12 @@ def workload(args):
 
 
 # ---------------------------------------------------------------- CPU oracle arm
-def oracle_sample(h, nrhs, seed):
-    """Time the oracle's factor + solve on the level-3 subtree; returns
-    (seconds, canonical flops of that sample)."""
+def oracle_sample(h, nrhs, seed, level):
+    """Time the oracle's factor + solve on the subtree under node 0 of `level`
+    (level 0: the whole matrix); returns (seconds, canonical flops, order)."""
     from oracle import ulv as O
     from paper_2311_00921_gb300 import inputs as I
-    hs = subtree(h, SAMPLE_LEVEL, 0)
+    hs = subtree(h, level, 0) if level > 0 else h
     b = I.rhs(hs.n, nrhs, seed)
     t0 = time.perf_counter()
     F = O.factor(hs)
@@ -213,15 +220,15 @@ def run_reference(args):
     w = workload(args)
     h = I.cached_build(w, os.environ.get("HSS_INPUT_CACHE"))
     for _ in range(args.warmup):
-        oracle_sample(h, w.nrhs, w.seed + 1)
+        oracle_sample(h, w.nrhs, w.seed + 1, REFERENCE_LEVEL)
     tot_t, tot_f = 0.0, 0.0
     n_s = 0
     for _ in range(args.steps):
-        dt, fl, n_s = oracle_sample(h, w.nrhs, w.seed + 1)
+        dt, fl, n_s = oracle_sample(h, w.nrhs, w.seed + 1, REFERENCE_LEVEL)
         tot_t += dt
         tot_f += fl
     val = tot_f / tot_t / 1e12
-    sample = (f"oracle factor+solve of the subtree under one level-{SAMPLE_LEVEL} node "
+    sample = (f"oracle factor+solve of the subtree under one level-{REFERENCE_LEVEL} node "
               f"(N={n_s}, leaf {w.leaf}, rank {w.rank}, {w.nrhs} rhs) of the {w.name} matrix")
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -229,8 +236,8 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "rank": w.rank,
                       "levels": w.levels, "nrhs": w.nrhs, "precision": "fp64"},
-           "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(),
-                            "kind": "oracle", "sample": sample},
+           "cpu_baseline": dict({"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                                 "kind": "oracle", "sample": sample}, **host_description()),
            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -287,7 +294,7 @@ PEAK_SOURCE = {"pair32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured 
                        "algorithmic product, so frac <= 1/3)"}
 
 
-def timed_steps(torch, dev, b, x, prec, steps, clocks=None, residual="fp64"):
+def timed_steps(torch, dev, b, x, prec, steps, clocks=None, residual="fp64", serialize=False):
     """K timed factor+solve steps on the current stream; returns a dict."""
     def step():
         dev.factorize(prec, residual=residual)
@@ -296,7 +303,7 @@ def timed_steps(torch, dev, b, x, prec, steps, clocks=None, residual="fp64"):
     if clocks:
         clocks.start()
         time.sleep(0.3)
-    dev.trace(True)
+    dev.trace(True, serialize=serialize)
     l0 = dev.launch_count()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
@@ -320,7 +327,14 @@ def timed_steps(torch, dev, b, x, prec, steps, clocks=None, residual="fp64"):
     return out
 
 
-def roofline_of(tr, peaks, steps, prec_mode="fp64"):
+PREC_LABEL = {"f64": "FP64", "f32": "FP32", "tf32": "TF32 x3", "bf16": "BF16 x3",
+              "pair32": "pair-of-FP32"}
+
+
+def roofline_of(tr, peaks, steps, prec_mode="fp64", overlapped=None):
+    """Roofline of the dominant kernel class of trace `tr` (a serialized pass:
+    every logged duration is the kernel's own).  `overlapped` is the trace of the
+    run as timed (basis chain concurrent on a second stream), reported beside it."""
     dom = max(tr, key=lambda k: tr[k][0])
     dms, dn, dfl = tr[dom]
     kind, prec = dom.split(".")
@@ -333,15 +347,21 @@ def roofline_of(tr, peaks, steps, prec_mode="fp64"):
         prec = "pair32"
         peak = peaks["f32"] / PAIR_OPS_PER_FLOP if peaks else None
     total = sum(v[0] for v in tr.values())
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if peak else None,
-            "traffic": traffic_record(kname) if prec == "f64" else None,
-            "kernel": f"{kname} ({ {'f64': 'FP64', 'f32': 'FP32', 'tf32': 'TF32 x3', 'bf16': 'BF16 x3', 'pair32': 'pair-of-FP32'}.get(prec, prec)})",
-            "peak_source": PEAK_SOURCE.get(prec),
-            "kernel_ms_per_launch": dms / max(1, dn), "kernel_share": dms / total,
-            "per_kernel_ms_per_step": {k: v[0] / steps for k, v in sorted(tr.items())},
-            "per_kernel_tflops": {k: (v[2] / (v[0] / 1e3) / 1e12 if v[0] else 0.0)
-                                  for k, v in sorted(tr.items())}}
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": (achieved / peak) if peak else None,
+           "traffic": traffic_record(kname, prec),
+           "kernel": f"{kname} ({PREC_LABEL.get(prec, prec)})",
+           "peak_source": PEAK_SOURCE.get(prec),
+           "timing": "serialized pass (basis chain on the main stream), CUDA events per launch",
+           "kernel_ms_per_launch": dms / max(1, dn), "kernel_launches_per_step": dn / steps,
+           "kernel_share": dms / total,
+           "per_kernel_ms_per_step": {k: v[0] / steps for k, v in sorted(tr.items())},
+           "per_kernel_tflops": {k: (v[2] / (v[0] / 1e3) / 1e12 if v[0] else 0.0)
+                                 for k, v in sorted(tr.items())}}
+    if overlapped:
+        out["per_kernel_ms_per_step_overlapped"] = {k: v[0] / steps
+                                                    for k, v in sorted(overlapped.items())}
+    return out
 
 
 def replica_workload(base, rank):
@@ -367,6 +387,26 @@ def job_tflops(world, flops_per_step, ms_per_step):
     return world * flops_per_step / (ms_per_step / 1e3) / 1e12
 
 
+def host_description():
+    """CPU model (lscpu / /proc/cpuinfo) and NumPy's BLAS, for the CPU baseline."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    blas = None
+    try:
+        cfg = np.__config__.CONFIG["Build Dependencies"]["blas"]
+        blas = f"{cfg.get('name')} {cfg.get('version')}".strip()
+    except Exception:
+        pass
+    return {"cpu_model": model, "blas": blas, "numpy": np.__version__}
+
+
 def run_ours(args):
     import torch
     from paper_2311_00921_gb300 import hss, inputs as I
@@ -390,6 +430,11 @@ def run_ours(args):
     fl_step = factor_flops(w.levels, w.leaf, w.rank) + solve_flops(w.levels, w.leaf, w.rank,
                                                                     w.nrhs)
 
+    def rel_residual(xv):
+        r = b - dev.matvec(xv)
+        return (torch.linalg.vector_norm(r, dim=0)
+                / torch.linalg.vector_norm(b, dim=0)).max().item()
+
     resid = args.residual if prec != "fp64" else "fp64"
     for _ in range(args.warmup):
         dev.factorize(prec, residual=resid)
@@ -402,43 +447,48 @@ def run_ours(args):
     ms_step = ms / args.steps
     value = job_tflops(world, fl_step, ms_step)
     # correctness of the timed result: FP64 residual through the HSS matvec
-    r = b - dev.matvec(x)
-    rel = (torch.linalg.vector_norm(r, dim=0) / torch.linalg.vector_norm(b, dim=0)).max().item()
+    rel = rel_residual(x)
     logdet = dev.logdet()
     x_head = x.clone()
+    # the same configuration once more with the basis chain serialized, so that
+    # every kernel's logged time is its own (the roofline's denominator)
+    nser = min(args.steps, 5)
+    ser = timed_steps(torch, dev, b, x, prec, nser, residual=resid, serialize=True)
 
-    # the same mixed path with the refinement residual in FP64 (for comparison)
-    mixed_r64 = None
-    if resid != "fp64" and not args.no_fp64_compare:
+    def variant(p, r_mode):
         for _ in range(2):
-            dev.factorize(prec, residual="fp64")
+            dev.factorize(p, residual=r_mode)
             dev.solve(b, x)
-        g = timed_steps(torch, dev, b, x, prec, args.steps, residual="fp64")
-        rr = b - dev.matvec(x)
-        mixed_r64 = {"ms_per_step": g["ms"] / args.steps, "factor_ms": g["factor_ms"],
-                     "solve_ms": g["solve_ms"],
-                     "max_rel_residual": (torch.linalg.vector_norm(rr, dim=0)
-                                          / torch.linalg.vector_norm(b, dim=0)).max().item(),
-                     "ir_iterations": g["info"]["ir_iters"]}
+        g = timed_steps(torch, dev, b, x, p, args.steps, residual=r_mode)
+        m = g["ms"] / args.steps
+        out = {"precision": p, "residual": r_mode, "ms_per_step": m,
+               "value": fl_step / (m / 1e3) / 1e12, "unit": "TFLOP/s",
+               "factor_ms": g["factor_ms"], "solve_ms": g["solve_ms"],
+               "max_rel_residual": rel_residual(x)}
+        if p != "fp64":
+            out["ir_iterations"] = g["info"]["ir_iters"]
+        out["max_rel_diff_vs_headline_x"] = (
+            torch.linalg.vector_norm(x_head - x, dim=0)
+            / torch.linalg.vector_norm(x_head, dim=0)).max().item()
+        return out, g
 
+    variants = {}
     fp64 = None
-    if prec != "fp64" and not args.no_fp64_compare:
-        for _ in range(2):
-            dev.factorize("fp64")
-            dev.solve(b, x)
-        f = timed_steps(torch, dev, b, x, "fp64", args.steps)
-        r64 = b - dev.matvec(x)
-        rel64 = (torch.linalg.vector_norm(r64, dim=0)
-                 / torch.linalg.vector_norm(b, dim=0)).max().item()
-        diff = (torch.linalg.vector_norm(x_head - x, dim=0)
-                / torch.linalg.vector_norm(x, dim=0)).max().item()
-        fp64 = {"ms_per_step": f["ms"] / args.steps, "factor_ms": f["factor_ms"],
-                "solve_ms": f["solve_ms"],
-                "value": fl_step / (f["ms"] / args.steps / 1e3) / 1e12, "unit": "TFLOP/s",
-                "max_rel_residual": rel64, "logdet": dev.logdet(),
-                "mixed_vs_fp64_max_rel_diff": diff,
-                "speedup_of_headline": (f["ms"] / args.steps) / ms_step,
-                "roofline": roofline_of(f["trace"], peaks, args.steps)}
+    if not args.no_variants:
+        if prec != "fp64":
+            other = "pair32" if resid == "fp64" else "fp64"
+            variants[f"{prec}_{other}_residual"] = variant(prec, other)[0]
+            for p in ("tf32", "bf16", "fp32"):
+                if p != prec:
+                    variants[f"{p}_fp64_residual"] = variant(p, "fp64")[0]
+        if prec != "fp64":
+            v64, g64 = variant("fp64", "fp64")
+            ser64 = timed_steps(torch, dev, b, x, "fp64", min(args.steps, 3), serialize=True)
+            v64["logdet"] = dev.logdet()
+            v64["headline_speedup_vs_fp64"] = v64["ms_per_step"] / ms_step
+            v64["roofline"] = roofline_of(ser64["trace"], peaks, min(args.steps, 3), "fp64",
+                                          overlapped=g64["trace"])
+            fp64 = v64
 
     e2e = None
     if not args.no_e2e:
@@ -446,12 +496,17 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        dt, fl, n_s = oracle_sample(h, w.nrhs, w.seed + 1)
+        dt, fl, n_s = oracle_sample(h, w.nrhs, w.seed + 1, SAMPLE_LEVEL)
         cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
                "kind": "oracle",
                "sample": f"oracle FP64 factor+solve of the subtree under one level-{SAMPLE_LEVEL}"
                          f" node (N={n_s}, same leaf/rank/kernel, {w.nrhs} rhs), "
                          f"{dt:.1f} s"}
+        cpu.update(host_description())
+    if rank == 0 and args.cpu_full and world == 1:
+        dt, fl, n_s = oracle_sample(h, w.nrhs, w.seed + 1, 0)
+        cpu = dict(cpu or {}, full_matrix={"seconds": dt, "value": fl / dt / 1e12,
+                                           "unit": "TFLOP/s", "n": n_s})
 
     if rank == 0:
         info = head["info"]
@@ -463,9 +518,10 @@ def run_ours(args):
                "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "rank": w.rank,
                           "levels": w.levels, "nrhs": w.nrhs,
                           "precision": prec if prec == "fp64" else
-                          f"{prec} factor + iterative refinement to 1e-12 (FP64 iterate "
-                          f"and test; residual in "
-                          f"{'pair-of-FP32, 48-bit' if resid == 'pair32' else 'FP64'})",
+                          f"{prec} factor + iterative refinement to 1e-12 (residual HSS "
+                          f"matvec, update and test in "
+                          f"{'pair-of-FP32 (48-bit) / FP64' if resid == 'pair32' else 'FP64'}"
+                          f"; root Cholesky FP64)",
                           "residual": resid,
                           "parallelism": f"replicas{world}" if world > 1 else "single",
                           "l2": "HSS data (1.54 GB) and factors exceed L2; no flush",
@@ -475,8 +531,9 @@ def run_ours(args):
                "factor_ms": head["factor_ms"], "solve_ms": head["solve_ms"],
                "check": {"max_rel_residual": rel, "logdet": logdet,
                          "ir_iterations": info["ir_iters"], "ir_resid": info["ir_resid"]},
-               "fp64": fp64, "mixed_fp64_residual": mixed_r64,
-               "roofline": roofline_of(head["trace"], peaks, args.steps, prec),
+               "fp64": fp64, "variants": variants,
+               "roofline": roofline_of(ser["trace"], peaks, nser, prec,
+                                       overlapped=head["trace"]),
                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
                "gpu_launches": head["launches"]}
         print(json.dumps(out), flush=True)
@@ -609,9 +666,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "tf32", "bf16", "fp32"],
                     help="factor arithmetic; non-fp64 modes refine in FP64 to 1e-12")
-    ap.add_argument("--residual", default="pair32", choices=["fp64", "pair32"],
+    ap.add_argument("--residual", default="fp64", choices=["fp64", "pair32"],
                     help="arithmetic of the refinement residual of the mixed modes")
-    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other precisions / residuals and the FP64 path")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time the oracle once on the whole matrix (about 100 s at N=2^18)")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched uneven workload with this many matrices instead")
     ap.add_argument("--workload", default=WORKLOAD)

@@ -56,9 +56,10 @@ extern "C" {
 typedef struct hss_s* hss_t;
 
 /* Arithmetic of the factorization.  HSS_FP64 computes every step in FP64.
- * The mixed modes compute the per-level steps (Alg. 2 lines 2-4) in lower
- * precision and use the factor as the preconditioner of FP64 iterative
- * refinement in hss_solve; the root Cholesky, residual and update are FP64.
+ * The mixed modes compute the per-level steps of Alg. 2 (diagonal product,
+ * partial Cholesky, merge) in lower precision and use the factor as the
+ * preconditioner of FP64 iterative refinement in hss_solve; the root
+ * Cholesky, residual and update are FP64.
  * HSS_MIXED_FP32: every per-level step in FP32 (FP32 accumulation).
  * HSS_MIXED_TF32 / HSS_MIXED_BF16: as FP32, but the two dense contractions of
  * the diagonal product (W = A V and A - Y'Vᵀ - V Y'ᵀ) run on the tensor cores
@@ -91,11 +92,18 @@ typedef struct {
 typedef enum { HSS_RESIDUAL_FP64 = 0, HSS_RESIDUAL_PAIR32 = 1 } hss_residual;
 
 typedef struct {
-  int32_t precision; /* hss_precision */
-  int32_t ir_max_it; /* refinement iteration limit (mixed modes), e.g. 30 */
-  double ir_tol;     /* stop when every column has ‖b - A x‖₂ / ‖b‖₂ <= ir_tol */
-  int32_t residual;  /* hss_residual (mixed modes) */
-  int32_t reserved;  /* 0 */
+  int32_t precision;   /* hss_precision */
+  int32_t ir_max_it;   /* refinement iteration limit (mixed modes), e.g. 30 */
+  double ir_tol;       /* stop when every column has ‖b - A x‖₂ / ‖b‖₂ <= ir_tol */
+  int32_t residual;    /* hss_residual (mixed modes) */
+  int32_t reserved;    /* 0 */
+  int64_t wait_budget; /* polls a device-side pipeline wait makes before it gives up and
+                          the call reports HSS_ERR_TIMEOUT (at the next synchronizing
+                          call); 0 = the default, 2^24 polls.  A negative value makes
+                          every such wait give up at once: a way to exercise the failure
+                          path.  The final wait of a kernel for tensor-core work it has
+                          already issued always uses the default, so that tensor memory
+                          is never released under a pending MMA. */
 } hss_options;
 
 /* Create a device-resident HSS object from its generators (format above).
@@ -173,7 +181,10 @@ int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t l
  * (one right-hand-side column); larger ones return HSS_ERR_TOO_LARGE before any
  * device work.  Columns are processed in passes of as many as fit (at most 32).
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every call
+ * device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process, so do not call this entry point
+ * again after a cudaDeviceReset (or any other teardown of the device's primary
+ * context): the module may then be loaded at another address.  Every call
  * shares the one array and overwrites all of the part it reads, so no state
  * carries over between calls -- but two calls that overlap on the GPU (other
  * streams, other host threads) race on it: serialize them.
@@ -225,7 +236,12 @@ typedef enum {
 /* Per-kernel timing: with enable = 1 every later launch of the object is
  * bracketed by two CUDA events on its launch stream and logged with its
  * algorithmic flop count (the operation's definition, not the executed
- * instructions); enable = 0 stops logging.  Enabling clears the log. */
+ * instructions); enable = 0 stops logging.  Enabling clears the log.
+ * enable = 2 logs as 1 and also serializes the factorization: the basis
+ * completion chain, which otherwise runs ahead on the object's second stream,
+ * runs on the caller's stream, so that every logged duration is the kernel's
+ * own and not shared with a concurrent kernel (for roofline accounting; the
+ * results are the same). */
 int hss_trace(hss_t h, int32_t enable);
 
 /* Sum of the logged launches of one kernel class (0 .. 2*HSS_K_COUNT-1; classes

@@ -13,14 +13,15 @@ It follows the paper step by step, one node at a time, with library primitives
   B = Q [0; L_B] (LAPACK's dgeqlf convention), computed here as the QR of the
   row- and column-reversed basis.  Q^S has exactly the span of B; L_B = Q^Sᵀ B
   is r x r lower triangular.
-* diagonal product, Alg. 2 line 2 / Eq. dense-split: Â = Qᵀ A_i Q.
-* partial Cholesky, Eq. partial-Cholesky (Alg. 2 line 3): L^RR = chol(Â^RR),
+* diagonal product (the first step of Alg. 2's node loop, Eq. dense-split):
+  Â = Qᵀ A_i Q.
+* partial Cholesky, Eq. partial-Cholesky (Alg. 2): L^RR = chol(Â^RR),
   L^SR = Â^SR L^RR⁻ᵀ (reading of the garbled second line), Â^SS -= L^SR L^SRᵀ.
-* merge, Alg. 2 line 4: the parent of siblings (c1, c2) gets
+* merge (Alg. 2, after each level): the parent of siblings (c1, c2) gets
   [[Â^SS_c1, Ŝᵀ], [Ŝ, Â^SS_c2]] with Ŝ = L_B(c2) S L_B(c1)ᵀ, and the basis
   blkdiag(L_B(c1), L_B(c2)) E_p.  (The skeleton coordinates change from Ũ to
   Q^S, which rescales the coupling and the transfer by L_B.)
-* root Cholesky, Alg. 2 line 6.
+* root Cholesky, the last step of Alg. 2.
 * factorized form and solve, Eq. hss-ulv-final-form and the solve that follows
   it (Sec. 3.2), read as ordered products; U^F is applied transposed on the way
   down and plain on the way up.
@@ -137,7 +138,7 @@ class ULVFactor:
 
 def node_step(A, B, dtype=np.float64, level=-1, node=-1):
     """One node of Alg. 2: basis completion (Eq. 2-3), diagonal product
-    Â = Qᵀ A Q (line 2) and partial Cholesky (line 3, Eq. partial-Cholesky).
+    Â = Qᵀ A Q and partial Cholesky (Eq. partial-Cholesky).
     Returns (Q, L_B, Â, L^RR, L^SR, Â^SS)."""
     A = np.asarray(A, dtype=dtype)
     B = np.asarray(B, dtype=dtype)
@@ -176,7 +177,7 @@ def factor(h, dtype=np.float64) -> ULVFactor:
             F.Q[l].append(Q); F.LB[l].append(LB); F.LRR[l].append(LRR)
             F.LSR[l].append(LSR); F.SS[l].append(SS); F.Ahat[l].append(Ah)
             F.Anode[l].append(A); F.Bnode[l].append(B)
-        # merge (Alg. 2 line 4): parents at level l-1
+        # merge (Alg. 2): parents at level l-1
         newA, newB = [], []
         for p in range(2 ** (l - 1)):
             c1, c2 = 2 * p, 2 * p + 1
@@ -189,7 +190,7 @@ def factor(h, dtype=np.float64) -> ULVFactor:
         A_lvl, B_lvl = newA, newB
     A0 = np.asarray(A_lvl[0], dtype=np.float64)              # root stays FP64
     F.A0 = A0
-    F.L0 = _chol(A0, 0, 0)                                   # Alg. 2 line 6
+    F.L0 = _chol(A0, 0, 0)                                   # root Cholesky of Alg. 2
     return F
 
 

@@ -86,6 +86,7 @@ struct hss_s {
   TcMode tc_mode = TcMode::TF32x3;
   int ir_max_it = 30;
   double ir_tol = 1e-12;
+  long long wait_budget = 0;           // polls of a device pipeline wait (0 = default)
   int residual = HSS_RESIDUAL_FP64;    // arithmetic of the refinement residual
   // pair-of-FP32 generators (hi parts are the FP32 factor's converted copies)
   // and the pair matvec's vectors, in the FP32 arena
@@ -105,6 +106,7 @@ struct hss_s {
   // launch accounting and the optional per-launch event log
   long long launches = 0;
   int tracing = 0;
+  int serialize = 0;                   // run the basis chain on the caller's stream
   struct Rec {
     int kind;
     double flops;
@@ -326,7 +328,7 @@ template <typename T>
 int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) {
   const int L = h->L, r = h->rank;
   const long long rr = (long long)r * r;
-  cudaStream_t qs = h->qstream;
+  cudaStream_t qs = h->serialize ? st : h->qstream;
   if (cudaEventRecord(h->ev_start, st) != cudaSuccess) return HSS_ERR_CUDA;
   if (cudaStreamWaitEvent(qs, h->ev_start, 0) != cudaSuccess) return HSS_ERR_CUDA;
   if constexpr (std::is_same<T, float>::value) {
@@ -386,7 +388,7 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
         tc = true;
         Launch k(h, HSS_K_TC_GEMM, 2.0 * b * r * (double)b * n, st);
         if (tc_gemm(h->tc_mode, b, r, b, Ain, b, bb, P.V, b, br, /*b_ncontig=*/false, f.W, b, br,
-                    n, h->status, st) != cudaSuccess)
+                    n, h->status, h->wait_budget, st) != cudaSuccess)
           return HSS_ERR_CUDA;
       }
     }
@@ -400,7 +402,7 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
       if constexpr (std::is_same<T, float>::value) {
         Launch k(h, HSS_K_TC_SYR2K, 2.0 * r * b * (b + 1.0) * n, st);
         if (tc_syr2k_lower(h->tc_mode, b, r, Ain, b, bb, f.Y, b, br, P.V, b, br, P.M, b, bb, n,
-                           h->status, st) != cudaSuccess)
+                           h->status, h->wait_budget, st) != cudaSuccess)
           return HSS_ERR_CUDA;
       }
     } else {
@@ -438,7 +440,7 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
   return HSS_OK;
 }
 
-// Blocked right-looking Cholesky of the FP64 root block (Alg. 2 line 6): a
+// Blocked right-looking Cholesky of the FP64 root block (last step of Alg. 2): a
 // one-CTA panel step (diagonal block and the rows below it) and a many-CTA
 // GEMM for the trailing update, so the 2r x 2r root is not bound to one SM.
 int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
@@ -487,7 +489,7 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
     }
     root = h->R0;
   }
-  // root Cholesky (Alg. 2 line 6), FP64 in every mode
+  // root Cholesky (last step of Alg. 2), FP64 in every mode
   const int b0 = 2 * r;
   int rc = root_cholesky(h, root, b0, st);
   if (rc) return rc;
@@ -949,6 +951,9 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     h->ir_max_it = opt->ir_max_it;
     h->ir_tol = opt->ir_tol;
     h->residual = opt->residual;
+    h->wait_budget = opt->wait_budget;
+  } else {
+    h->wait_budget = 0;
   }
   h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
   h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;
@@ -1043,12 +1048,13 @@ int hss_last_info(hss_t h, int32_t* level, int32_t* node, int32_t* col, int32_t*
 }
 
 int hss_trace(hss_t h, int32_t enable) {
-  if (!h) return HSS_ERR_INVALID_ARG;
+  if (!h || enable < 0 || enable > 2) return HSS_ERR_INVALID_ARG;
   if (enable) {
     for (auto& r : h->trace) cudaEventSynchronize(r.b);
     clear_trace(h);
   }
   h->tracing = enable ? 1 : 0;
+  h->serialize = enable == 2 ? 1 : 0;
   return HSS_OK;
 }
 

@@ -1,5 +1,5 @@
 // Tensor-core (tcgen05, sm_103a) GEMM for the dense contractions of the
-// diagonal product in the mixed-precision factorization (Alg. 2 line 2 in the
+// diagonal product in the mixed-precision factorization (Alg. 2, in the
 // compact-WY form): W = A V and the rank-2r update A - Y'Vᵀ - V Y'ᵀ.
 //
 // One CTA (4 warps) owns a 128 x 128 output tile; the accumulator lives in
@@ -15,7 +15,10 @@
 // TMEM lanes) and writes alpha·acc + beta·C_in, optionally only on and below
 // the diagonal.  Every mbarrier wait is bounded: on expiry the kernel records
 // HSS_ERR_TIMEOUT in the status word, stops issuing, waits (bounded) for the
-// MMAs already issued, frees its tensor memory and returns.
+// MMAs already issued, frees its tensor memory and returns.  The pipeline
+// waits poll at most `wait_limit` times (set by the caller; 0 polls = give up
+// at once); the final wait for issued MMAs always uses the long default, so
+// that tensor memory is never released under a pending MMA.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -29,7 +32,7 @@ namespace {
 constexpr int TM = 128, TN = 128, TK = 32;   // CTA tile and K slab (elements)
 constexpr int TC_THREADS = 128;
 constexpr uint32_t kTmemCols = 128;
-constexpr long long kWaitLimit = 1LL << 24;   // polls before a wait gives up
+constexpr long long kWaitLimit = 1LL << 24;   // default polls before a wait gives up
 
 HSS_DEVINL uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -51,8 +54,8 @@ HSS_DEVINL uint32_t make_idesc(uint32_t ab_format, int m, int n) {
          ((uint32_t)(m >> 4) << 24);
 }
 
-HSS_DEVINL bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+HSS_DEVINL bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -130,7 +133,7 @@ template <typename E, int NPASS>
 __global__ void __launch_bounds__(TC_THREADS)
 tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const float* Cin,
                int ldcin, long long sCin, float* C, int ldc, long long sC, int lower_only,
-               int tiles_m, int* status) {
+               int tiles_m, int* status, long long wait_limit) {
   constexpr int NSLAB = (NPASS == 3) ? 4 : 2;                  // A hi/lo, B hi/lo
   constexpr uint32_t SLAB = TM * TK * sizeof(E);               // bytes per slab
   constexpr uint32_t STAGE = NSLAB * SLAB;
@@ -178,7 +181,8 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
     const int s = kc & 1;
     unsigned char* st = smem + s * STAGE;
     if (kc >= 2) {   // the MMAs that read this stage two slabs ago are done
-      if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kc >> 1) - 1) & 1))) abort_s = 1;
+      if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kc >> 1) - 1) & 1), wait_limit))
+        abort_s = 1;
       __syncthreads();
       if (abort_s) break;
     }
@@ -225,7 +229,8 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
   // wait for every issued MMA (commit tracks all earlier MMAs of the thread)
   if (tid == 0 && issued > 0) {
     const int last = issued - 1;
-    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) abort_s = 2;
+    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), kWaitLimit))
+      abort_s = 2;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -274,7 +279,7 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
 template <typename E, int NPASS>
 cudaError_t launch(int M, int N, const Term& t1, const Term& t2, float alpha, float beta,
                    const float* Cin, int ldcin, long long sCin, float* C, int ldc, long long sC,
-                   bool lower, int batch, int* status, cudaStream_t st) {
+                   bool lower, int batch, int* status, long long wait_limit, cudaStream_t st) {
   constexpr int NSLAB = (NPASS == 3) ? 4 : 2;
   // at least 57 KB so that no more than 4 CTAs (4 x 128 TMEM columns) share an SM
   const size_t smem = std::max<size_t>(2 * (size_t)NSLAB * TM * TK * sizeof(E), 57 * 1024);
@@ -289,7 +294,8 @@ cudaError_t launch(int M, int N, const Term& t1, const Term& t2, float alpha, fl
   const int tiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
   dim3 g(tiles, 1, batch);
   tc_gemm_kernel<E, NPASS><<<g, TC_THREADS, smem, st>>>(M, N, t1, t2, alpha, beta, Cin, ldcin, sCin,
-                                                       C, ldc, sC, lower ? 1 : 0, tiles_m, status);
+                                                       C, ldc, sC, lower ? 1 : 0, tiles_m, status,
+                                                       wait_limit);
   return cudaGetLastError();
 }
 
@@ -297,14 +303,16 @@ cudaError_t launch(int M, int N, const Term& t1, const Term& t2, float alpha, fl
 
 cudaError_t tc_gemm(TcMode mode, int M, int N, int K, const float* A, int lda, long long sA,
                     const float* B, int ldb, long long sB, bool b_ncontig, float* C, int ldc,
-                    long long sC, int batch, int* status, cudaStream_t st) {
+                    long long sC, int batch, int* status, long long wait_budget,
+                    cudaStream_t st) {
+  const long long wl = wait_budget > 0 ? wait_budget : (wait_budget < 0 ? 0 : kWaitLimit);
   Term t1{A, lda, sA, true, B, ldb, sB, b_ncontig, K};
   Term t2{A, lda, sA, true, B, ldb, sB, b_ncontig, 0};
   switch (mode) {
-    case TcMode::TF32: return launch<float, 1>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, st);
-    case TcMode::TF32x3: return launch<float, 3>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, st);
-    case TcMode::BF16: return launch<__nv_bfloat16, 1>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, st);
-    case TcMode::BF16x3: return launch<__nv_bfloat16, 3>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, st);
+    case TcMode::TF32: return launch<float, 1>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
+    case TcMode::TF32x3: return launch<float, 3>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
+    case TcMode::BF16: return launch<__nv_bfloat16, 1>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
+    case TcMode::BF16x3: return launch<__nv_bfloat16, 3>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -312,16 +320,17 @@ cudaError_t tc_gemm(TcMode mode, int M, int N, int K, const float* A, int lda, l
 cudaError_t tc_syr2k_lower(TcMode mode, int m, int k, const float* A, int lda, long long sA,
                            const float* P, int ldp, long long sP, const float* Q, int ldq,
                            long long sQ, float* Mout, int ldm, long long sM, int batch, int* status,
-                           cudaStream_t st) {
+                           long long wait_budget, cudaStream_t st) {
+  const long long wl = wait_budget > 0 ? wait_budget : (wait_budget < 0 ? 0 : kWaitLimit);
   // Mout = A - (P Qᵀ + Q Pᵀ) on and below the diagonal: two terms along K,
   // operand A = P then Q (row-contiguous), operand B(n, k) = Q(n, k) then P(n, k)
   Term t1{P, ldp, sP, true, Q, ldq, sQ, true, k};
   Term t2{Q, ldq, sQ, true, P, ldp, sP, true, k};
   switch (mode) {
-    case TcMode::TF32: return launch<float, 1>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, st);
-    case TcMode::TF32x3: return launch<float, 3>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, st);
-    case TcMode::BF16: return launch<__nv_bfloat16, 1>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, st);
-    case TcMode::BF16x3: return launch<__nv_bfloat16, 3>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, st);
+    case TcMode::TF32: return launch<float, 1>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
+    case TcMode::TF32x3: return launch<float, 3>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
+    case TcMode::BF16: return launch<__nv_bfloat16, 1>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
+    case TcMode::BF16x3: return launch<__nv_bfloat16, 3>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -6,12 +6,12 @@
 //                         Q = I - V T Vᵀ = [Q^R Q^S] with the redundant part first,
 //                         and L_B = Q^Sᵀ B (r x r, lower triangular).
 //  * chol_panel_kernel -- one 32-column panel of the partial Cholesky, Eq.
-//                         partial-Cholesky (Alg. 2 line 3), for every node of a
+//                         partial-Cholesky (Alg. 2), for every node of a
 //                         level: POTRF of the diagonal block and TRSM of the rows
 //                         below it; the trailing SYRK is a level-wide launch
 //                         (gemm.cu).  With c = b it is the panel of the root
-//                         Cholesky (line 6).
-//  * scatter_ss_kernel -- the merge (Alg. 2 line 4): Â^SS of each node into its
+//                         Cholesky (the last step of Alg. 2).
+//  * scatter_ss_kernel -- the merge (Alg. 2): Â^SS of each node into its
 //                         parent's diagonal block.
 //  * pchol_kernel      -- the whole partial Cholesky of a node in one CTA, with
 //                         the merge as its epilogue (the batched forest path).
@@ -1124,7 +1124,7 @@ cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, dou
 }
 
 // Â^SS of every node (lower triangle at M[c:, c:]) into its parent's diagonal
-// block at (off, off), both triangles (the merge of Alg. 2 line 4)
+// block at (off, off), both triangles (the merge step of Alg. 2)
 template <typename T>
 __global__ void scatter_ss_kernel(const T* __restrict__ Mb, int ldm, long long sM, int c, int r,
                                   T* PA, int ldpa, long long sPA) {

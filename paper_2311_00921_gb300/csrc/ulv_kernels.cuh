@@ -55,7 +55,7 @@ cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, dou
                               int level, int node0, int col0, int* status, int nodes,
                               bool accumulate, cudaStream_t st);
 
-// The merge of Alg. 2 line 4 as its own pass: Â^SS of node i (lower triangle
+// The merge step of Alg. 2 as its own pass: Â^SS of node i (lower triangle
 // of M[c:, c:], r x r) into block (i & 1) of parent i / 2's diagonal, both triangles.
 template <typename T>
 cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T* PA, int ldpa,

@@ -33,7 +33,7 @@ class Shape(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("ir_max_it", ctypes.c_int32),
                 ("ir_tol", ctypes.c_double), ("residual", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("wait_budget", ctypes.c_int64)]
 
 
 RESIDUALS = {"fp64": 0, "pair32": 1}
@@ -167,10 +167,13 @@ class HSS:
             pass
 
     def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, residual="fp64",
-                  stream=None):
+                  stream=None, wait_budget=0):
         """residual: arithmetic of the refinement residual of the mixed modes,
-        "fp64" or "pair32" (pairs of FP32 numbers, 48-bit significands)."""
-        opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual], 0)
+        "fp64" or "pair32" (pairs of FP32 numbers, 48-bit significands).
+        wait_budget: polls of a device-side pipeline wait (0 = default, < 0 =
+        give up at once)."""
+        opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual], 0,
+                      wait_budget)
         _check(load().hss_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_factorize")
         self.precision = precision
@@ -233,8 +236,11 @@ class HSS:
     KERNELS = ("ql", "gemm", "gemm_skinny", "syr2k", "pchol", "trsv_fwd", "trsv_bwd", "other",
                "tc_gemm", "tc_syr2k", "pair_gemm")
 
-    def trace(self, enable: bool):
-        _check(load().hss_trace(self._h, 1 if enable else 0), "hss_trace")
+    def trace(self, enable: bool, serialize: bool = False):
+        """Per-launch event timing on/off; serialize also runs the basis chain on
+        the caller's stream so that each logged time is the kernel's own."""
+        mode = (2 if serialize else 1) if enable else 0
+        _check(load().hss_trace(self._h, mode), "hss_trace")
 
     def trace_read(self):
         """{"kernel.f64" / "kernel.f32": (ms, launches, algorithmic flops)} of the
@@ -322,7 +328,7 @@ class HSSBatch:
             pass
 
     def factorize(self, stream=None):
-        opt = Options(HSS_FP64, 0, 0.0, 0, 0)
+        opt = Options(HSS_FP64, 0, 0.0, 0, 0, 0)
         _check(load().hss_batch_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_batch_factorize")
 

@@ -322,3 +322,78 @@ def test_per_step_fp32_factor(levels, leaf, rank):
                             f"L^RR32 l={l} i={i}")
             check_close(np.tril(M[i][c:, c:]), np.tril(F.SS[l][i]).astype(np.float64), 1e-3,
                         f"SS32 l={l} i={i}")
+
+
+@pytest.mark.slow
+def test_per_step_fp32_factor_wide_tiles():
+    """The FP32 factor at the benchmark's node shape (leaf 512, rank 128) with 128
+    leaves, so that the wide FP32 tile (128 x 128, engaged from 2 x 152 tiles per
+    launch) and the 128-row tiles of the leaf products run, per step against the
+    oracle's float32 factor: basis completion, L^RR and Â^SS of every node of
+    every level.  Same bounds as the small FP32 per-step test."""
+    w = I.scaled(I.WORKLOADS["sphere_yukawa_256k"], 65536)
+    h = I.build_hss(w)
+    assert h.levels == 7 and h.leaf == 512 and h.rank == 128
+    dev = hss.HSS(h)
+    dev.factorize("fp32")
+    dev.sync()
+    F = O.factor(h, dtype=np.float32)
+    for l in range(h.levels, 0, -1):
+        V, T, LB, M = (dev.export(k, l) for k in ("V", "T", "LB", "M"))
+        for i in range(2 ** l):
+            b, r = V.shape[1], V.shape[2]
+            c = b - r
+            check_close(q_from_vt(V[i], T[i]), F.Q[l][i].astype(np.float64), 2e-4,
+                        f"Q32 l={l} i={i}")
+            check_close(LB[i], F.LB[l][i].astype(np.float64), 2e-4, f"L_B32 l={l} i={i}")
+            check_close(np.tril(M[i][:c, :c]), F.LRR[l][i].astype(np.float64), 1e-3,
+                        f"L^RR32 l={l} i={i}")
+            check_close(M[i][c:, :c], F.LSR[l][i].astype(np.float64), 1e-3,
+                        f"L^SR32 l={l} i={i}")
+            check_close(np.tril(M[i][c:, c:]), np.tril(F.SS[l][i]).astype(np.float64), 1e-3,
+                        f"SS32 l={l} i={i}")
+
+
+def _extreme_eigs(dev, n, its=60, seed=0):
+    """λ_max by power iteration on the HSS matvec and λ_min by power iteration
+    on the FP64 factor's solve (inverse iteration); both on the GPU."""
+    rng = np.random.default_rng(seed)
+    v = hss.colmajor(rng.standard_normal((n, 1)))
+    lam_max = 0.0
+    for _ in range(its):
+        v = v / torch.linalg.vector_norm(v)
+        av = dev.matvec(v)
+        lam_max = float((v * av).sum())
+        v = av
+    v = hss.colmajor(rng.standard_normal((n, 1)))
+    mu = 0.0
+    for _ in range(its):
+        v = v / torch.linalg.vector_norm(v)
+        iv = dev.solve(v)
+        mu = float((v * iv).sum())
+        v = iv
+    return lam_max, 1.0 / mu
+
+
+@pytest.mark.slow
+def test_grid_exp_full_size_against_oracle():
+    """The geostatistics workload at its stated size: N = 65,536 jittered grid,
+    exp(-d/0.1) + 1e-4 I, leaf 512, rank 128, 7 levels, 8 right-hand sides, FP64.
+    x within 1e-10 per column and log det within 1e-12 of Σ|2 log l_jj| against
+    the oracle, backward residual at round-off, and the condition number
+    estimated on the GPU (printed; the 1e-10 target assumes κ ε well below it)."""
+    w = I.WORKLOADS["grid_exp_64k"]
+    h = I.build_hss(w)
+    assert (h.n, h.levels, h.leaf, h.rank) == (65536, 7, 512, 128)
+    dev, F, b, x = run_both(h, w.nrhs, seed=w.seed + 1)
+    lam_max, lam_min = _extreme_eigs(dev, h.n)
+    kappa = lam_max / lam_min
+    x_ref = O.solve(F, b)
+    err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    res = b - O.matvec(h, x)
+    rel = np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)
+    print(f"grid_exp_64k: kappa ~ {kappa:.3e} (lambda_max {lam_max:.4e}, lambda_min "
+          f"{lam_min:.4e}); x rel err max {err.max():.3e}; residual max {rel.max():.3e}; "
+          f"logdet {dev.logdet():.10e} vs oracle {O.logdet(F):.10e}")
+    assert rel.max() <= 1e-13, rel.max()
+    check_end_to_end(dev, F, b, x)

@@ -3,14 +3,16 @@ device memory when they call the library (their device memory is reserved up
 front by a host pool, or a cudaMalloc is not allowed in their loop).  It keeps
 its per-level vectors in a fixed static device array instead of a workspace.
 
-Checked here through the C ABI against the allocating hss_matvec, on two calls
-in a row (the static array is shared and keeps the previous call's contents),
-with the tolerance of the other matvec tests; and the size limit.  This file is
-collected last so that a failure here comes after every other test has run.
+Checked here through the C ABI against the allocating hss_matvec and against
+the oracle's HSS matvec, on two calls in a row (the static array is shared and
+keeps the previous call's contents), with the tolerance of the other matvec
+tests; and the size limit.  This file is collected last so that a failure here
+comes after every other test has run.
 """
 import numpy as np
 import pytest
 
+from oracle import ulv as O
 from paper_2311_00921_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -33,6 +35,7 @@ def on_device(arrays):
 @pytest.mark.parametrize("levels,leaf,rank,nrhs", [
     (4, 80, 24, 35),     # 32 columns per pass: two passes, ragged second
     (9, 128, 128, 12),   # 8 columns per pass fit the static array: two passes
+    (1, 96, 20, 3),      # one level: no transfer matrices, E unused
 ])
 def test_noalloc_matvec_matches_allocating_matvec_twice(levels, leaf, rank, nrhs):
     h = I.random_hss(levels, leaf, rank, seed=levels + rank, orthonormal=False)
@@ -45,7 +48,9 @@ def test_noalloc_matvec_matches_allocating_matvec_twice(levels, leaf, rank, nrhs
         y = torch.full((nrhs, h.n), float("nan"), dtype=torch.float64, device="cuda").t()
         hss.matvec_noalloc(shape, D, U, E, S, x, y)
         torch.cuda.synchronize()
-        assert rel_err(y.cpu().numpy(), y_ref) <= 1e-13, f"call {call}"
+        y = y.cpu().numpy()
+        assert rel_err(y, y_ref) <= 1e-13, f"call {call}"
+        assert rel_err(y, O.matvec(h, x.cpu().numpy()).reshape(y.shape)) <= 1e-13, f"call {call}"
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
