@@ -182,7 +182,8 @@ KERNEL_SOURCES = {"tc_gemm": "tc_gemm_kernel", "tc_syr2k": "tc_gemm_kernel",
                   "pchol": "pchol_kernel", "ql": "ql_basis_kernel",
                   "gemm_skinny": "gemm_n16_kernel", "trsv_fwd": "trsv_fwd_kernel",
                   "trsv_bwd": "trsv_bwd_kernel", "other": "logdet_reduce_kernel",
-                  "pair_gemm": "df_gemm_kernel"}
+                  "pair_gemm": "df_gemm_kernel", "basis_gemm": "basis_gemm_kernel",
+                  "basis_node": "recon_lu_kernel"}
 # pair-of-FP32 arithmetic: 12 FP32 instructions per multiply-add (2 flops) plus a
 # 3-instruction renormalisation every 4 terms
 PAIR_OPS_PER_FLOP = 12.75 / 2

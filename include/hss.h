@@ -91,12 +91,24 @@ typedef struct {
  * The update x += d and the convergence test stay FP64. */
 typedef enum { HSS_RESIDUAL_FP64 = 0, HSS_RESIDUAL_PAIR32 = 1 } hss_residual;
 
+/* Method of the basis completion (Eq. 2-3); both give the same V, T and L_B up
+ * to rounding (the Householder QL with LAPACK's dlarfg signs).
+ * HSS_BASIS_AUTO: Cholesky QR twice of the reversed basis as level-wide
+ * products, then the Householder vectors reconstructed from the orthonormal
+ * factor by an unpivoted LU of its top block (one CTA per node); nodes whose
+ * Gram matrix is not numerically positive definite in the working precision,
+ * and ranks too large for the per-node kernels (above 165 in FP64, 234 in
+ * FP32), use the Householder kernel.
+ * HSS_BASIS_HOUSEHOLDER: the Householder kernel (one CTA per node, a
+ * CTA-wide reduction per column) for every node. */
+typedef enum { HSS_BASIS_AUTO = 0, HSS_BASIS_HOUSEHOLDER = 1 } hss_basis_method;
+
 typedef struct {
   int32_t precision;   /* hss_precision */
   int32_t ir_max_it;   /* refinement iteration limit (mixed modes), e.g. 30 */
   double ir_tol;       /* stop when every column has ‖b - A x‖₂ / ‖b‖₂ <= ir_tol */
   int32_t residual;    /* hss_residual (mixed modes) */
-  int32_t reserved;    /* 0 */
+  int32_t basis;       /* hss_basis_method: how the basis completion is computed */
   int64_t wait_budget; /* polls a device-side pipeline wait makes before it gives up and
                           the call reports HSS_ERR_TIMEOUT (at the next synchronizing
                           call); 0 = the default, 2^24 polls.  A negative value makes
@@ -218,7 +230,7 @@ int hss_export(hss_t h, int32_t what, int32_t level, double* dst, size_t count);
 
 /* Kernel classes reported by the tracer (one per kernel function). */
 typedef enum {
-  HSS_K_QL = 0,        /* basis completion (Householder QL + compact-WY T) */
+  HSS_K_QL = 0,        /* basis completion by the Householder kernel (QL + compact-WY T) */
   HSS_K_GEMM = 1,      /* batched GEMM, 64x64 tiles (diagonal product, merge) */
   HSS_K_GEMM_SKINNY = 2, /* batched GEMM with <= 32 columns (solve, matvec) */
   HSS_K_SYR2K = 3,     /* lower-triangle rank-2k update (diagonal product) */
@@ -229,8 +241,10 @@ typedef enum {
   HSS_K_TC_GEMM = 8,   /* tensor-core (tcgen05) W = A V of the mixed diagonal product */
   HSS_K_TC_SYR2K = 9,  /* tensor-core (tcgen05) rank-2r update of the mixed diagonal product */
   HSS_K_PAIR_GEMM = 10, /* pair-of-FP32 GEMM of the refinement residual (logged as FP32) */
-  HSS_K_COUNT = 11,
-  HSS_K_FP32 = 11      /* added to a class: the same kernel run in FP32 (mixed modes) */
+  HSS_K_BASIS_GEMM = 11, /* level-wide products of the basis completion (Cholesky QR, reconstruction) */
+  HSS_K_BASIS_NODE = 12, /* per-node Cholesky / LU / triangular inverses of the basis completion */
+  HSS_K_COUNT = 13,
+  HSS_K_FP32 = 13      /* added to a class: the same kernel run in FP32 (mixed modes) */
 } hss_kernel_kind;
 
 /* Per-kernel timing: with enable = 1 every later launch of the object is

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/hss.h"
+#include "basis.cuh"
 #include "common.cuh"
 #include "dfgemm.cuh"
 #include "ir_kernels.cuh"
@@ -51,6 +52,7 @@ struct Factor {
   const T *D = nullptr, *U = nullptr, *E = nullptr, *S = nullptr;   // generators in T
   T *Dc = nullptr, *Uc = nullptr, *Ec = nullptr, *Sc = nullptr;     // converted copies (float)
   T* d = nullptr;               // n x kSolveCols refinement correction (float)
+  BasisScratch<T> bs;           // scratch of the basis completion chain
   void* arena = nullptr;
   size_t bytes = 0;
 };
@@ -88,6 +90,7 @@ struct hss_s {
   double ir_tol = 1e-12;
   long long wait_budget = 0;           // polls of a device pipeline wait (0 = default)
   int residual = HSS_RESIDUAL_FP64;    // arithmetic of the refinement residual
+  int basis_method = HSS_BASIS_AUTO;   // method of the basis completion
   // pair-of-FP32 generators (hi parts are the FP32 factor's converted copies)
   // and the pair matvec's vectors, in the FP32 arena
   float *Dl = nullptr, *Ul = nullptr, *El = nullptr, *Sl = nullptr;
@@ -159,6 +162,11 @@ void layout_factor(Bump& bp, Factor<T>& f, int L, int leaf, int r) {
   f.Z = bp.take<T>(nL * r * r);
   f.t1 = bp.take<T>(nL * r * kSolveCols);
   f.t2 = bp.take<T>(nL * r * kSolveCols);
+  // the basis chain runs concurrently with the main chain: its own scratch
+  f.bs.X = bp.take<T>(nL * leaf * r);
+  for (T** p : {&f.bs.G, &f.bs.R1, &f.bs.R, &f.bs.P, &f.bs.U, &f.bs.Ui})
+    *p = bp.take<T>(nL * r * r);
+  f.bs.fail = bp.take<int>(nL);
 }
 
 // the object's main arena: FP64 generators, FP64 factor, matvec and refinement
@@ -282,6 +290,38 @@ struct Launch {
   }
 };
 
+// Hooks of the basis completion chain: the same accounting as Launch, opened
+// before and closed after each of its launches.
+struct BasisTrace {
+  hss_s* h;
+  cudaStream_t st;
+  bool f32;
+  hss_s::Rec rec{};
+  bool on = false;
+};
+
+void basis_before(void* ctx, int kind, double flops) {
+  BasisTrace* t = static_cast<BasisTrace*>(ctx);
+  ++t->h->launches;
+  t->on = false;
+  if (!t->h->tracing) return;
+  static const int cls[4] = {HSS_K_BASIS_GEMM, HSS_K_BASIS_NODE, HSS_K_OTHER, HSS_K_QL};
+  t->rec.kind = cls[kind] + (t->f32 ? HSS_K_FP32 : 0);
+  t->rec.flops = flops;
+  if (cudaEventCreate(&t->rec.a) == cudaSuccess && cudaEventCreate(&t->rec.b) == cudaSuccess) {
+    cudaEventRecord(t->rec.a, t->st);
+    t->on = true;
+  }
+}
+
+void basis_after(void* ctx) {
+  BasisTrace* t = static_cast<BasisTrace*>(ctx);
+  if (!t->on) return;
+  cudaEventRecord(t->rec.b, t->st);
+  t->h->trace.push_back(t->rec);
+  t->on = false;
+}
+
 void clear_trace(hss_s* h) {
   for (auto& r : h->trace) {
     cudaEventDestroy(r.a);
@@ -342,7 +382,17 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
     const long long br = (long long)b * r;
     // (a) basis completion (Eq. 2-3)
     const T* Bsrc = (l == L) ? f.U : P.B;
-    {
+    if (h->basis_method == HSS_BASIS_AUTO && r <= basis_max_rank<T>()) {
+      // Cholesky QR twice + Householder reconstruction; Householder kernel for
+      // the nodes it flags
+      BasisTrace bt{h, qs, sizeof(T) == 4};
+      BasisHook hook;
+      hook.before = basis_before;
+      hook.after = basis_after;
+      hook.ctx = &bt;
+      HSS_TRY(launch_basis_completion<T>(Bsrc, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, f.bs,
+                                         hook, qs));
+    } else {
       Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, qs,
                sizeof(T) == 4);
       HSS_TRY(launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, qs));
@@ -426,11 +476,16 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
       if (nt > 0) {
         Launch k(h, HSS_K_SYR2K, (double)nt * (nt + 1.0) * kb * n, st, sizeof(T) == 4);
         T* Tr = Mk + kb + (long long)kb * b;
-        syrk_lower_batched<T>(nt, kb, Tr, b, bb, Mk + kb, b, bb, Tr, b, bb, n, st);
+        if (k0 + kb == c)   // the last update leaves Â^SS: its epilogue is the merge
+          syrk_lower_merge_batched<T>(nt, kb, Tr, b, bb, Mk + kb, b, bb, Tr, b, bb, Q.A, ldq, sq,
+                                      n, st);
+        else
+          syrk_lower_batched<T>(nt, kb, Tr, b, bb, Mk + kb, b, bb, Tr, b, bb, n, st);
       }
     }
-    // (d, second half) Â^SS into the parents' diagonal blocks
-    {
+    // (d, second half) with nothing eliminated (c = 0) Â^SS is the whole block:
+    // copied into the parents' diagonal blocks by its own pass
+    if (c == 0) {
       Launch k(h, HSS_K_OTHER, 0.0, st, sizeof(T) == 4);
       HSS_TRY(launch_scatter_ss<T>(P.M, b, bb, c, r, Q.A, ldq, sq, n, st));
     }
@@ -941,6 +996,8 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
   if (opt && (opt->ir_max_it < 0 || !(opt->ir_tol >= 0.0))) return HSS_ERR_INVALID_ARG;
   if (opt && opt->residual != HSS_RESIDUAL_FP64 && opt->residual != HSS_RESIDUAL_PAIR32)
     return HSS_ERR_INVALID_ARG;
+  if (opt && opt->basis != HSS_BASIS_AUTO && opt->basis != HSS_BASIS_HOUSEHOLDER)
+    return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
   if (prec != HSS_FP64) {
@@ -952,8 +1009,10 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     h->ir_tol = opt->ir_tol;
     h->residual = opt->residual;
     h->wait_budget = opt->wait_budget;
+    h->basis_method = opt->basis;
   } else {
     h->wait_budget = 0;
+    h->basis_method = HSS_BASIS_AUTO;
   }
   h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
   h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;

@@ -64,6 +64,14 @@ void syr2k_lower_batched(int m, int k, const T* A, int lda, long long sA,
                          const T* P, int ldp, long long sP, const T* Q, int ldq, long long sQ,
                          T* M, int ldm, long long sM, int batch, cudaStream_t st);
 
+// As syrk_lower_batched, and the result of node z (both triangles) also goes to
+// the diagonal block at offset (z & 1) m of parent block z / 2 of PA (ld ldpa,
+// stride sPA): the merge step of Alg. 2 fused into the last Schur update.
+template <typename T>
+void syrk_lower_merge_batched(int m, int k, const T* A, int lda, long long sA, const T* P,
+                              int ldp, long long sP, T* M, int ldm, long long sM, T* PA, int ldpa,
+                              long long sPA, int batch, cudaStream_t st);
+
 // M(i, j) = A(i, j) - sum_k P(i,k) P(j,k) on the lower triangle; A may alias M.
 template <typename T>
 void syrk_lower_batched(int m, int k, const T* A, int lda, long long sA, const T* P, int ldp,

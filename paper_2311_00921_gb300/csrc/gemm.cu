@@ -466,11 +466,14 @@ void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA
 
 // lower-triangle tiles only: blockIdx.x enumerates tile pairs (ti >= tj).
 // SYRK = true: M = A - P Pᵀ (Q unused); else M = A - (P Qᵀ + Q Pᵀ).
-template <typename T, bool SYRK = false>
+// MERGE (with SYRK): the result of node z is also written, both triangles, into
+// diagonal block z & 1 (offset (z & 1) m) of parent block z / 2 of PA (ld ldpa,
+// stride sPA): the merge of Alg. 2 as the epilogue of the last Schur update.
+template <typename T, bool SYRK = false, bool MERGE = false>
 __global__ void __launch_bounds__(NT)
 syr2k_lower_kernel(int m, int k, const T* A, int lda, long long sA, const T* __restrict__ P,
                    int ldp, long long sP, const T* __restrict__ Q, int ldq, long long sQ, T* M,
-                   int ldm, long long sM) {
+                   int ldm, long long sM, T* PA = nullptr, int ldpa = 0, long long sPA = 0) {
   __shared__ T Pi[BK][BM + 1], Qi[BK][BM + 1], Pj[BK][BN + 1], Qj[BK][BN + 1];
   const long long bz = blockIdx.y;
   A += bz * sA;
@@ -538,7 +541,14 @@ syr2k_lower_kernel(int m, int k, const T* A, int lda, long long sA, const T* __r
     for (int p = 0; p < 4; ++p) {
       const int gi = i0 + tx + 16 * p;
       if (gi >= m || gi < gj) continue;
-      M[gi + (long long)gj * ldm] = A[gi + (long long)gj * lda] - acc[p][q];
+      const T v = A[gi + (long long)gj * lda] - acc[p][q];
+      M[gi + (long long)gj * ldm] = v;
+      if (MERGE) {
+        T* pa = PA + (bz >> 1) * sPA;
+        const int off = (int)(bz & 1) * m;
+        pa[(off + gi) + (long long)(off + gj) * ldpa] = v;
+        if (gi != gj) pa[(off + gj) + (long long)(off + gi) * ldpa] = v;
+      }
     }
   }
 }
@@ -585,6 +595,24 @@ void syrk_lower_batched(int m, int k, const T* A, int lda, long long sA, const T
                                                 sM);
 }
 
+template <typename T>
+void syrk_lower_merge_batched(int m, int k, const T* A, int lda, long long sA, const T* P,
+                              int ldp, long long sP, T* M, int ldm, long long sM, T* PA, int ldpa,
+                              long long sPA, int batch, cudaStream_t st) {
+  if (m <= 0 || batch <= 0) return;
+  const int nt = (m + BM - 1) / BM;
+  dim3 g(nt * (nt + 1) / 2, batch);
+  syr2k_lower_kernel<T, true, true><<<g, NT, 0, st>>>(m, k, A, lda, sA, P, ldp, sP, P, ldp, sP, M,
+                                                      ldm, sM, PA, ldpa, sPA);
+}
+
+template void syrk_lower_merge_batched<double>(int, int, const double*, int, long long,
+                                               const double*, int, long long, double*, int,
+                                               long long, double*, int, long long, int,
+                                               cudaStream_t);
+template void syrk_lower_merge_batched<float>(int, int, const float*, int, long long, const float*,
+                                              int, long long, float*, int, long long, float*, int,
+                                              long long, int, cudaStream_t);
 template void syrk_lower_batched<double>(int, int, const double*, int, long long, const double*,
                                          int, long long, double*, int, long long, int,
                                          cudaStream_t);

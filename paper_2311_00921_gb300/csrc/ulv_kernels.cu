@@ -11,8 +11,11 @@
 //                         below it; the trailing SYRK is a level-wide launch
 //                         (gemm.cu).  With c = b it is the panel of the root
 //                         Cholesky (the last step of Alg. 2).
-//  * scatter_ss_kernel -- the merge (Alg. 2): Â^SS of each node into its
-//                         parent's diagonal block.
+//  * scatter_ss_kernel -- the merge (Alg. 2) as its own pass: Â^SS of each node
+//                         into its parent's diagonal block.  Used only where a
+//                         level eliminates nothing (rank = block order); otherwise
+//                         the last Schur update writes the parent block itself
+//                         (syrk_lower_merge_batched, gemm.cu).
 //  * pchol_kernel      -- the whole partial Cholesky of a node in one CTA, with
 //                         the merge as its epilogue (the batched forest path).
 //  * trsv_fwd_kernel /
@@ -106,7 +109,8 @@ HSS_DEVINL void cta_vt_times(const T* Pt, const T* A, long long lda, int ncols, 
 template <typename T, int NBP, int RPT>
 __global__ void __launch_bounds__(NT)
 ql_basis_kernel(const T* __restrict__ Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
-                long long sT, T* LB, long long sL, int b, int r) {
+                long long sT, T* LB, long long sL, int b, int r, const int* __restrict__ only_if) {
+  if (only_if && only_if[blockIdx.x] == 0) return;   // node completed by another path
   extern __shared__ unsigned char smem_raw[];
   T* Pt = reinterpret_cast<T*>(smem_raw);       // panel reflectors, transposed: (NBP+1) x b
   T* Ws = Pt + (size_t)b * (NBP + 1);           // NBP x r : Ṽ_pᵀ A_trail
@@ -1077,26 +1081,26 @@ size_t ql_smem(int b, int r) {
 template <typename T, int NBP, int RPT>
 cudaError_t launch_ql_rows(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                            long long sT, T* LB, long long sL, int b, int r, int nodes,
-                           cudaStream_t st) {
+                           cudaStream_t st, const int* only_if) {
   const size_t sm = ql_smem<T>(b, r);
   if (!smem_opt_in(ql_basis_kernel<T, NBP, RPT>, sm)) return cudaErrorInvalidConfiguration;
   ql_basis_kernel<T, NBP, RPT><<<nodes, NT, sm, st>>>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL,
-                                                      b, r);
+                                                      b, r, only_if);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                             long long sT, T* LB, long long sL, int b, int r, int nodes,
-                            cudaStream_t st) {
+                            cudaStream_t st, const int* only_if) {
   // panel width: 16 columns in FP64, 32 in FP32; RPT panel rows per thread
   constexpr int NBP = sizeof(T) == 8 ? 16 : 32;
   if (b > 3 * NT || r > 256) return cudaErrorInvalidValue;
   if (b <= NT)
-    return launch_ql_rows<T, NBP, 1>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st);
+    return launch_ql_rows<T, NBP, 1>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st, only_if);
   if (b <= 2 * NT)
-    return launch_ql_rows<T, NBP, 2>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st);
-  return launch_ql_rows<T, NBP, 3>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st);
+    return launch_ql_rows<T, NBP, 2>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st, only_if);
+  return launch_ql_rows<T, NBP, 3>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st, only_if);
 }
 
 template <typename T>
@@ -1232,7 +1236,8 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
 
 #define INST(T)                                                                                  \
   template cudaError_t launch_ql_basis<T>(const T*, int, long long, T*, long long, T*, long long,  \
-                                          T*, long long, int, int, int, cudaStream_t);            \
+                                          T*, long long, int, int, int, cudaStream_t,             \
+                                          const int*);                                             \
   template cudaError_t launch_pchol<T>(T*, int, long long, int, int, T*, int, long long, double*, \
                                        int, int, int*, int, cudaStream_t);                        \
   template cudaError_t launch_trsv_fwd<T>(const T*, int, long long, int, int, T*, int, long long, \

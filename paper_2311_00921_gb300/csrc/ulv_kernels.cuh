@@ -2,9 +2,12 @@
 #pragma once
 #include <cuda_runtime.h>
 
+// Householder QL basis completion, one CTA per node.  only_if (n flags, may be
+// null): complete only the nodes whose flag is nonzero.
 template <typename T>
 cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
-                     long long sT, T* LB, long long sL, int b, int r, int nodes, cudaStream_t st);
+                            long long sT, T* LB, long long sL, int b, int r, int nodes,
+                            cudaStream_t st, const int* only_if = nullptr);
 
 template <typename T>
 size_t pchol_smem(int b);

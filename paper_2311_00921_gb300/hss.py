@@ -33,10 +33,11 @@ class Shape(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("ir_max_it", ctypes.c_int32),
                 ("ir_tol", ctypes.c_double), ("residual", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("wait_budget", ctypes.c_int64)]
+                ("basis", ctypes.c_int32), ("wait_budget", ctypes.c_int64)]
 
 
 RESIDUALS = {"fp64": 0, "pair32": 1}
+BASIS_METHODS = {"auto": 0, "householder": 1}
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -167,13 +168,14 @@ class HSS:
             pass
 
     def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, residual="fp64",
-                  stream=None, wait_budget=0):
+                  stream=None, wait_budget=0, basis="auto"):
         """residual: arithmetic of the refinement residual of the mixed modes,
         "fp64" or "pair32" (pairs of FP32 numbers, 48-bit significands).
         wait_budget: polls of a device-side pipeline wait (0 = default, < 0 =
-        give up at once)."""
-        opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual], 0,
-                      wait_budget)
+        give up at once).  basis: "auto" (Cholesky QR + reconstruction) or
+        "householder" (the method of the basis completion)."""
+        opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual],
+                      BASIS_METHODS[basis], wait_budget)
         _check(load().hss_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_factorize")
         self.precision = precision
@@ -234,7 +236,7 @@ class HSS:
                 "ir_iters": it.value, "ir_resid": res.value}
 
     KERNELS = ("ql", "gemm", "gemm_skinny", "syr2k", "pchol", "trsv_fwd", "trsv_bwd", "other",
-               "tc_gemm", "tc_syr2k", "pair_gemm")
+               "tc_gemm", "tc_syr2k", "pair_gemm", "basis_gemm", "basis_node")
 
     def trace(self, enable: bool, serialize: bool = False):
         """Per-launch event timing on/off; serialize also runs the basis chain on

@@ -397,3 +397,63 @@ def test_grid_exp_full_size_against_oracle():
           f"logdet {dev.logdet():.10e} vs oracle {O.logdet(F):.10e}")
     assert rel.max() <= 1e-13, rel.max()
     check_end_to_end(dev, F, b, x)
+
+
+# ---------------------------------------------------------------- basis completion methods
+@pytest.mark.parametrize("levels,leaf,rank", [(3, 100, 13), (2, 256, 64)])
+def test_householder_basis_method(levels, leaf, rank):
+    """The Householder kernel (hss_options.basis = HOUSEHOLDER) per step and end
+    to end against the oracle, like the default method."""
+    h = I.random_hss(levels, leaf, rank, seed=levels * 13 + leaf, orthonormal=False)
+    dev = hss.HSS(h)
+    dev.factorize("fp64", basis="householder")
+    F = O.factor(h)
+    b = I.rhs(h.n, 3, 7)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    check_steps(dev, F, h)
+    check_end_to_end(dev, F, b, x)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ill_conditioned_basis_falls_back_to_householder(prec):
+    """A leaf basis with two columns parallel to 1e-9: its Gram matrix is not
+    numerically positive definite, so that node (and only that node) is completed
+    by the Householder kernel -- its V and T are bit for bit those of the
+    Householder method -- and the solve still matches the oracle."""
+    h = I.random_hss(3, 64, 16, seed=91, orthonormal=False)
+    rng = np.random.default_rng(5)
+    h.U[5][:, 1] = h.U[5][:, 0] * (1.0 + 1e-9) + 1e-9 * rng.standard_normal(64)
+    auto, ref = hss.HSS(h), hss.HSS(h)
+    auto.factorize(prec)
+    ref.factorize(prec, basis="householder")
+    auto.sync()
+    ref.sync()
+    L = h.levels
+    Va, Ta, Vr, Tr = auto.export("V", L), auto.export("T", L), ref.export("V", L), ref.export("T", L)
+    assert np.array_equal(Va[5], Vr[5]) and np.array_equal(Ta[5], Tr[5])
+    assert not np.array_equal(Va[4], Vr[4])           # a well-conditioned node: reconstruction
+    tol = 50 * 64 * (EPS if prec == "fp64" else 6e-8)
+    check_close(q_from_vt(Va[4], Ta[4]), q_from_vt(Vr[4], Tr[4]), tol, "Q node 4")
+    b = I.rhs(h.n, 2, 3)
+    x = auto.solve(hss.colmajor(b)).cpu().numpy()
+    x_ref = O.solve(O.factor(h), b)
+    err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    assert err.max() <= 1e-10, err
+
+
+def test_rank_above_the_per_node_limit():
+    """Rank 176 (block order 352 above the leaves): FP64 completes the bases with
+    the Householder kernel (the reconstruction's r x r block exceeds shared
+    memory), FP32 with the reconstruction; both per step against the oracle."""
+    h = I.random_hss(2, 256, 176, seed=176, orthonormal=False)
+    dev, F, b, x = run_both(h, 2)
+    check_steps(dev, F, h)
+    check_end_to_end(dev, F, b, x)
+    dev.factorize("fp32")
+    dev.sync()
+    F32 = O.factor(h, dtype=np.float32)
+    for l in range(h.levels, 0, -1):
+        V, T = dev.export("V", l), dev.export("T", l)
+        for i in range(2 ** l):
+            check_close(q_from_vt(V[i], T[i]), F32.Q[l][i].astype(np.float64), 2e-4,
+                        f"Q32 l={l} i={i}")
