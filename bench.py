@@ -332,7 +332,7 @@ PREC_LABEL = {"f64": "FP64", "f32": "FP32", "tf32": "TF32 x3", "bf16": "BF16 x3"
               "pair32": "pair-of-FP32"}
 
 
-def roofline_of(tr, peaks, steps, prec_mode="fp64", overlapped=None):
+def roofline_of(tr, peaks, steps, prec_mode="fp64", overlapped=None, overlapped_steps=None):
     """Roofline of the dominant kernel class of trace `tr` (a serialized pass:
     every logged duration is the kernel's own).  `overlapped` is the trace of the
     run as timed (basis chain concurrent on a second stream), reported beside it."""
@@ -360,7 +360,7 @@ def roofline_of(tr, peaks, steps, prec_mode="fp64", overlapped=None):
            "per_kernel_tflops": {k: (v[2] / (v[0] / 1e3) / 1e12 if v[0] else 0.0)
                                  for k, v in sorted(tr.items())}}
     if overlapped:
-        out["per_kernel_ms_per_step_overlapped"] = {k: v[0] / steps
+        out["per_kernel_ms_per_step_overlapped"] = {k: v[0] / (overlapped_steps or steps)
                                                     for k, v in sorted(overlapped.items())}
     return out
 
@@ -488,7 +488,7 @@ def run_ours(args):
             v64["logdet"] = dev.logdet()
             v64["headline_speedup_vs_fp64"] = v64["ms_per_step"] / ms_step
             v64["roofline"] = roofline_of(ser64["trace"], peaks, min(args.steps, 3), "fp64",
-                                          overlapped=g64["trace"])
+                                          overlapped=g64["trace"], overlapped_steps=args.steps)
             fp64 = v64
 
     e2e = None
@@ -534,7 +534,7 @@ def run_ours(args):
                          "ir_iterations": info["ir_iters"], "ir_resid": info["ir_resid"]},
                "fp64": fp64, "variants": variants,
                "roofline": roofline_of(ser["trace"], peaks, nser, prec,
-                                       overlapped=head["trace"]),
+                                       overlapped=head["trace"], overlapped_steps=args.steps),
                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
                "gpu_launches": head["launches"]}
         print(json.dumps(out), flush=True)
