@@ -440,6 +440,20 @@ def run_ours(args):
     for _ in range(args.warmup):
         dev.factorize(prec, residual=resid)
         dev.solve(b, x)
+    if args.profile_step:
+        # one step inside the profiler window (ncu --profile-from-start off):
+        # the launch list of exactly one factorization + solve
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        l0 = dev.launch_count()
+        dev.factorize(prec, residual=resid)
+        dev.solve(b, x)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_step": True, "precision": prec, "residual": resid,
+                          "workload": w.name, "gpu_launches": dev.launch_count() - l0,
+                          "max_rel_residual": rel_residual(x)}), flush=True)
+        return 0
     peaks = measured_peaks(torch) if rank == 0 else None
     if dist:
         dist.barrier()
@@ -671,6 +685,9 @@ def main():
                     help="arithmetic of the refinement residual of the mixed modes")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other precisions / residuals and the FP64 path")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run W warm-up steps, then one step between cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off) and exit")
     ap.add_argument("--cpu-full", action="store_true",
                     help="also time the oracle once on the whole matrix (about 100 s at N=2^18)")
     ap.add_argument("--batch", type=int, default=0,

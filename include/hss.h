@@ -103,19 +103,32 @@ typedef enum { HSS_RESIDUAL_FP64 = 0, HSS_RESIDUAL_PAIR32 = 1 } hss_residual;
  * CTA-wide reduction per column) for every node. */
 typedef enum { HSS_BASIS_AUTO = 0, HSS_BASIS_HOUSEHOLDER = 1 } hss_basis_method;
 
+/* Schedule of the solve's upper levels (the levels of at most 64 nodes above
+ * the leaves).  HSS_SCHEDULE_ASYNC: one launch per direction for all of them,
+ * with no barrier between levels (asynchronous execution of the tree, Sec. 4.2):
+ * going up, the CTA that finishes the second child of a node goes on with the
+ * node; going down, a cooperative launch in which each node waits for its
+ * parent's ready flag (a bounded wait, see wait_budget; an expired wait makes
+ * the solve report HSS_ERR_TIMEOUT).  HSS_SCHEDULE_LEVELS: one launch per level
+ * and direction.  Both give the same result. */
+typedef enum { HSS_SCHEDULE_ASYNC = 0, HSS_SCHEDULE_LEVELS = 1 } hss_schedule;
+
 typedef struct {
   int32_t precision;   /* hss_precision */
   int32_t ir_max_it;   /* refinement iteration limit (mixed modes), e.g. 30 */
   double ir_tol;       /* stop when every column has ‖b - A x‖₂ / ‖b‖₂ <= ir_tol */
   int32_t residual;    /* hss_residual (mixed modes) */
   int32_t basis;       /* hss_basis_method: how the basis completion is computed */
-  int64_t wait_budget; /* polls a device-side pipeline wait makes before it gives up and
-                          the call reports HSS_ERR_TIMEOUT (at the next synchronizing
-                          call); 0 = the default, 2^24 polls.  A negative value makes
+  int64_t wait_budget; /* polls a device-side wait (tensor-core pipeline, ready flags of
+                          the solve) makes before it gives up and the call reports
+                          HSS_ERR_TIMEOUT (at the next synchronizing call); 0 = the
+                          default, 2^24 polls.  A negative value makes
                           every such wait give up at once: a way to exercise the failure
                           path.  The final wait of a kernel for tensor-core work it has
                           already issued always uses the default, so that tensor memory
                           is never released under a pending MMA. */
+  int32_t schedule;    /* hss_schedule: how the solve's upper levels are launched */
+  int32_t reserved;    /* 0 */
 } hss_options;
 
 /* Create a device-resident HSS object from its generators (format above).

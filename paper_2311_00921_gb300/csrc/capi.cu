@@ -30,7 +30,8 @@ constexpr int kMaxCols = 32;      // right-hand-side columns per matvec pass
 constexpr int kSolveCols = 16;    // columns per triangular-sweep / refinement pass
 constexpr int kPanel = 32;        // columns per blocked-Cholesky panel (the panel kernel's limit)
 constexpr int kRootPanels = 16;
-constexpr int kFuseNodes = 64;     // levels up to this many nodes apply Q inside the sweep kernel   // log-det slots of the blocked root Cholesky (2r <= 512)
+constexpr int kFuseNodes = 64;    // levels up to this many nodes apply Q inside the sweep kernel
+constexpr int kTreeTop = 6;       // levels 1 .. 6 (<= 64 nodes): one tree launch per direction
 
 template <typename T>
 struct LevelT {
@@ -91,6 +92,10 @@ struct hss_s {
   long long wait_budget = 0;           // polls of a device pipeline wait (0 = default)
   int residual = HSS_RESIDUAL_FP64;    // arithmetic of the refinement residual
   int basis_method = HSS_BASIS_AUTO;   // method of the basis completion
+  int schedule = HSS_SCHEDULE_ASYNC;   // launches of the solve's upper levels
+  int* tree_cnt = nullptr;             // arrival counts of the tree forward sweep
+  int* tree_ready = nullptr;           // ready flags of the tree backward sweep
+  int tree_epoch = 0;
   // pair-of-FP32 generators (hi parts are the FP32 factor's converted copies)
   // and the pair matvec's vectors, in the FP32 arena
   float *Dl = nullptr, *Ul = nullptr, *El = nullptr, *Sl = nullptr;
@@ -102,6 +107,9 @@ struct hss_s {
   cudaStream_t qstream = nullptr;
   std::vector<cudaEvent_t> ev_level;
   cudaEvent_t ev_start = nullptr;
+  // the FP64 matvec's leaf product D x runs on its own stream beside the sweeps
+  cudaStream_t mstream = nullptr;
+  cudaEvent_t ev_mv_start = nullptr, ev_mv_dx = nullptr;
   double* zq64 = nullptr;              // merge scratch of the basis chain (n_L/2 x r x r)
   float* zq32 = nullptr;
   int ir_iters = 0;
@@ -212,6 +220,8 @@ size_t layout_main(hss_s* h, char* base) {
   h->logdet_part = bp.take<double>((size_t)(2 * nL - 1) + kRootPanels);
   h->logdet_val = bp.take<double>(1);
   h->status = bp.take<int>(8);
+  h->tree_cnt = bp.take<int>(size_t(2) << kTreeTop);
+  h->tree_ready = bp.take<int>(size_t(2) << kTreeTop);
   return bp.off + 256;
 }
 
@@ -598,7 +608,18 @@ void apply_q(hss_s* h, Factor<T>& f, const LevelT<T>& P, T* vec, int ldv, int nc
 template <typename T>
 int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) {
   const int L = h->L, r = h->rank;
-  for (int l = L; l >= 1; --l) {
+  // levels lo .. 1 (the narrow top of the tree) run as one launch per direction
+  const int lo = h->schedule == HSS_SCHEDULE_ASYNC ? std::min(L - 1, kTreeTop) : 0;
+  TreeLevels<T> tl{};
+  double tree_flops = 0.0;
+  for (int l = 0; l <= lo; ++l) {
+    tl.M[l] = f.lv[l].M;
+    tl.V[l] = f.lv[l].V;
+    tl.Tm[l] = f.lv[l].T_;
+    tl.vec[l] = f.lv[l].yv;
+    if (l >= 1) tree_flops += (trsv_flops(2 * r, r, nc) + qapply_flops(2 * r, r, nc)) * (1 << l);
+  }
+  for (int l = L; l > lo; --l) {
     LevelT<T>& P = f.lv[l];
     LevelT<T>& Q = f.lv[l - 1];
     T* vec = (l == L) ? x : P.yv;
@@ -614,6 +635,10 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     HSS_TRY(launch_ulv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
                               Q.n * Q.b, r, fused ? P.V : nullptr, (long long)P.b * r, P.T_,
                               (long long)r * r, r, P.n, st));
+  }
+  if (lo >= 1) {
+    Launch k(h, HSS_K_TRSV_FWD, tree_flops, st, sizeof(T) == 4);
+    HSS_TRY(launch_tree_fwd<T>(tl, lo, 2 * r, r, r, nc, h->tree_cnt, st));
   }
   const int b0 = 2 * r;
   double* rootA;
@@ -645,7 +670,14 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     Launch k(h, HSS_K_OTHER, 0.0, st);
     launch_f64_to_f32(rv, reinterpret_cast<float*>(f.lv[0].yv), (long long)b0 * nc, st);
   }
-  for (int l = 1; l <= L; ++l) {
+  if (lo >= 1) {
+    const long long wl = h->wait_budget > 0 ? h->wait_budget : (h->wait_budget < 0 ? 0 : 1LL << 24);
+    if (++h->tree_epoch <= 0) h->tree_epoch = 1;
+    Launch k(h, HSS_K_TRSV_BWD, tree_flops, st, sizeof(T) == 4);
+    HSS_TRY(launch_tree_bwd<T>(tl, lo, 2 * r, r, r, nc, h->tree_ready, h->tree_epoch, wl,
+                               h->status, st));
+  }
+  for (int l = lo + 1; l <= L; ++l) {
     LevelT<T>& P = f.lv[l];
     LevelT<T>& Q = f.lv[l - 1];
     T* vec = (l == L) ? x : P.yv;
@@ -670,10 +702,19 @@ int matvec_fp64(hss_s* h, const double* x, int ldx, double* y, int ldy, int nrhs
   const int L = h->L, r = h->rank, leaf = h->leaf;
   const long long rr = (long long)r * r;
   const int nL = 1 << L;
+  const cudaStream_t ms = h->serialize ? st : h->mstream;
   for (int j0 = 0; j0 < nrhs; j0 += kMaxCols) {
     const int nc = std::min(kMaxCols, nrhs - j0);
     const double* xc = x + (long long)j0 * ldx;
     double* yc = y + (long long)j0 * ldy;
+    // leaves, first part: y = D x, which needs nothing else, on the second
+    // stream while the basis sweeps below run on the caller's
+    if (cudaEventRecord(h->ev_mv_start, st) != cudaSuccess ||
+        cudaStreamWaitEvent(ms, h->ev_mv_start, 0) != cudaSuccess)
+      return HSS_ERR_CUDA;
+    gemm<double>(h, false, false, leaf, nc, leaf, 1.0, h->D, leaf, (long long)leaf * leaf, xc, ldx,
+                 leaf, 0.0, yc, ldy, leaf, nL, ms);
+    if (cudaEventRecord(h->ev_mv_dx, ms) != cudaSuccess) return HSS_ERR_CUDA;
     // up-sweep: x̂_L = Uᵀ x, x̂_l = E_lᵀ [x̂_{l+1}(2p); x̂_{l+1}(2p+1)]
     gemm<double>(h, true, false, r, nc, leaf, 1.0, h->U, leaf, (long long)leaf * r, xc, ldx, leaf,
                  0.0, h->xh[L], nL * r, r, nL, st);
@@ -693,9 +734,8 @@ int matvec_fp64(hss_s* h, const double* x, int ldx, double* y, int ldy, int nrhs
     for (int l = 1; l <= L - 1; ++l)
       gemm<double>(h, false, false, 2 * r, nc, r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, h->yh[l],
                    (1 << l) * r, r, 1.0, h->yh[l + 1], (2 << l) * r, 2 * r, 1 << l, st);
-    // leaves: y = D x + U ŷ
-    gemm<double>(h, false, false, leaf, nc, leaf, 1.0, h->D, leaf, (long long)leaf * leaf, xc, ldx,
-                 leaf, 0.0, yc, ldy, leaf, nL, st);
+    // leaves, second part: y += U ŷ once D x is done
+    if (cudaStreamWaitEvent(st, h->ev_mv_dx, 0) != cudaSuccess) return HSS_ERR_CUDA;
     gemm<double>(h, false, false, leaf, nc, r, 1.0, h->U, leaf, (long long)leaf * r, h->yh[L],
                  nL * r, r, 1.0, yc, ldy, leaf, nL, st);
     int rc = check_launch();
@@ -952,6 +992,7 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   if (L >= 2) e = e ? e : cudaMemcpy(h->E, E, sizeof(double) * h->esz, kind);
   e = e ? e : cudaMemcpy(h->S, S, sizeof(double) * h->ssz, kind);
   e = e ? e : cudaMemset(h->status, 0, 8 * sizeof(int));
+  e = e ? e : cudaMemset(h->tree_ready, 0, sizeof(int) << (kTreeTop + 1));
   if (e != cudaSuccess) {
     cudaFree(mem);
     delete h;
@@ -959,7 +1000,10 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   }
   h->ev_level.assign(L + 1, nullptr);
   e = cudaStreamCreateWithFlags(&h->qstream, cudaStreamNonBlocking);
+  e = e ? e : cudaStreamCreateWithFlags(&h->mstream, cudaStreamNonBlocking);
   e = e ? e : cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+  e = e ? e : cudaEventCreateWithFlags(&h->ev_mv_start, cudaEventDisableTiming);
+  e = e ? e : cudaEventCreateWithFlags(&h->ev_mv_dx, cudaEventDisableTiming);
   for (int l = 1; l <= L && e == cudaSuccess; ++l)
     e = cudaEventCreateWithFlags(&h->ev_level[l], cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -980,7 +1024,11 @@ void hss_destroy(hss_t h) {
   for (cudaEvent_t ev : h->ev_level)
     if (ev) cudaEventDestroy(ev);
   if (h->ev_start) cudaEventDestroy(h->ev_start);
+  if (h->ev_mv_start) cudaEventDestroy(h->ev_mv_start);
+  if (h->ev_mv_dx) cudaEventDestroy(h->ev_mv_dx);
+  if (h->mstream) cudaStreamSynchronize(h->mstream);
   if (h->qstream) cudaStreamDestroy(h->qstream);
+  if (h->mstream) cudaStreamDestroy(h->mstream);
   cudaFree(h->arena);
   if (h->f32.arena) cudaFree(h->f32.arena);
   cudaSetDevice(cur);
@@ -998,6 +1046,8 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     return HSS_ERR_INVALID_ARG;
   if (opt && opt->basis != HSS_BASIS_AUTO && opt->basis != HSS_BASIS_HOUSEHOLDER)
     return HSS_ERR_INVALID_ARG;
+  if (opt && opt->schedule != HSS_SCHEDULE_ASYNC && opt->schedule != HSS_SCHEDULE_LEVELS)
+    return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
   if (prec != HSS_FP64) {
@@ -1010,9 +1060,11 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     h->residual = opt->residual;
     h->wait_budget = opt->wait_budget;
     h->basis_method = opt->basis;
+    h->schedule = opt->schedule;
   } else {
     h->wait_budget = 0;
     h->basis_method = HSS_BASIS_AUTO;
+    h->schedule = HSS_SCHEDULE_ASYNC;
   }
   h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
   h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;

@@ -798,12 +798,21 @@ HSS_DEVINL void q_apply(T* y, T* yr, bool fill, int b, int nrhs, const T* V, con
   }
 }
 
-// forward: y (b x nrhs, smem) := [L^RR⁻¹ y^R ; y^S - L^SR L^RR⁻¹ y^R]
-template <typename T>
-__global__ void __launch_bounds__(NT)
-trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
-                long long sX, int nrhs, T* Par, int ldpar, long long sPar, const T* Vb,
-                long long sV, const T* Tb, long long sT, int r, int CB, int NBUF) {
+// a load of a vector that another CTA of the same kernel may have written:
+// through L2 (CG) so that no stale L1 line is read
+template <bool CG, typename T>
+HSS_DEVINL T ldv(const T* p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+
+// forward: y (b x nrhs, smem) := [L^RR⁻¹ y^R ; y^S - L^SR L^RR⁻¹ y^R], for node
+// `node` of the batch (one CTA)
+template <typename T, bool CG>
+HSS_DEVINL void fwd_node(int node, const T* __restrict__ Mb, int ldm, long long sM, int b, int c,
+                         T* X, int ldx, long long sX, int nrhs, T* Par, int ldpar, long long sPar,
+                         const T* Vb, long long sV, const T* Tb, long long sT, int r, int CB,
+                         int NBUF) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) T zt[NB * 16];
   T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs, ld = b
@@ -815,7 +824,6 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
   T* t1 = zpq + (size_t)NT * ZP;
   T* t2 = t1 + (size_t)16 * r;
   T* Lbuf = yr + qsz;                      // NBUF panels of P x CB
-  const int node = blockIdx.x;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
@@ -823,7 +831,7 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
   if (!Vb && nblk > 0) stage_panel(M, ldm, 0, min(CB, c), b, Lbuf, P);
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
-    y[i + j * b] = x[i + (long long)j * ldx];
+    y[i + j * b] = ldv<CG>(x + i + (long long)j * ldx);
   }
   if (Vb) {   // y := Qᵀ y, then the first panel
     __syncthreads();
@@ -909,13 +917,22 @@ trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
   }
 }
 
-// backward: x^S from the parent's vector (or in place when Par is null),
-// x^R = L^RR⁻ᵀ (z^R - L^SRᵀ x^S); the node segment becomes [x^R; x^S]
 template <typename T>
 __global__ void __launch_bounds__(NT)
-trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
-                long long sX, int nrhs, const T* Par, int ldpar, long long sPar, const T* Vb,
+trsv_fwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
+                long long sX, int nrhs, T* Par, int ldpar, long long sPar, const T* Vb,
                 long long sV, const T* Tb, long long sT, int r, int CB, int NBUF) {
+  fwd_node<T, false>(blockIdx.x, Mb, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, Vb, sV,
+                     Tb, sT, r, CB, NBUF);
+}
+
+// backward: x^S from the parent's vector (or in place when Par is null),
+// x^R = L^RR⁻ᵀ (z^R - L^SRᵀ x^S); the node segment becomes [x^R; x^S]
+template <typename T, bool CG>
+HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long sM, int b, int c,
+                         T* X, int ldx, long long sX, int nrhs, const T* Par, int ldpar,
+                         long long sPar, const T* Vb, long long sV, const T* Tb, long long sT,
+                         int r, int CB, int NBUF) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs
   const int P = b | 1;
@@ -925,7 +942,6 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
   T* t1 = zp + (size_t)NT * ZP;
   T* t2 = t1 + (size_t)16 * (Vb ? r : 0);
   T* Lbuf = t2 + (size_t)16 * (Vb ? r : 0);
-  const int node = blockIdx.x;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
@@ -939,9 +955,9 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
     const int i = e % b, j = e / b;
     T v;
     if (i >= c && Par)
-      v = Par[(long long)node * sPar + (i - c) + (long long)j * ldpar];
+      v = ldv<CG>(Par + (long long)node * sPar + (i - c) + (long long)j * ldpar);
     else
-      v = x[i + (long long)j * ldx];
+      v = ldv<CG>(x + i + (long long)j * ldx);
     y[i + j * b] = v;
   }
   __syncthreads();
@@ -1030,6 +1046,104 @@ trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     x[i + (long long)j * ldx] = y[i + j * b];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT)
+trsv_bwd_kernel(const T* __restrict__ Mb, int ldm, long long sM, int b, int c, T* X, int ldx,
+                long long sX, int nrhs, const T* Par, int ldpar, long long sPar, const T* Vb,
+                long long sV, const T* Tb, long long sT, int r, int CB, int NBUF) {
+  bwd_node<T, false>(blockIdx.x, Mb, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, Vb, sV,
+                     Tb, sT, r, CB, NBUF);
+}
+
+// ------------------------------------------------------------------ upper tree in one launch
+// Levels lo .. 1 of the solve (block order b = 2r at every level) in one
+// launch each way, without a barrier between levels: a node's step starts as
+// soon as the nodes it depends on are done (the asynchronous execution of the
+// tree of Sec. 4.2, within one GPU).
+//
+// Forward (leaves towards the root): CTA k starts with node k of level lo.
+// After a node, the CTA counts itself in at the parent; the CTA that arrives
+// second runs the parent (its sibling's results are already in memory), the
+// first one retires.  Nothing waits.
+template <typename T>
+__global__ void __launch_bounds__(NT)
+tree_fwd_kernel(TreeLevels<T> lv, int lo, int b, int c, int r, int nrhs, int* __restrict__ cnt,
+                int CB, int NBUF) {
+  __shared__ int go;
+  int l = lo, i = blockIdx.x;
+  for (;;) {
+    const int n = 1 << l;
+    fwd_node<T, true>(i, lv.M[l], b, (long long)b * b, b, c, lv.vec[l], n * b, b, nrhs,
+                      lv.vec[l - 1], (n / 2) * b, r, lv.V[l], (long long)b * r, lv.Tm[l],
+                      (long long)r * r, r, CB, NBUF);
+    if (l == 1) break;
+    __threadfence();   // this node's results before the arrival count
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      go = atomicAdd(cnt + (1 << (l - 1)) - 1 + (i >> 1), 1) == 1;
+      __threadfence();
+    }
+    __syncthreads();
+    if (!go) break;
+    --l;
+    i >>= 1;
+  }
+}
+
+HSS_DEVINL int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+HSS_DEVINL void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Backward (root towards the leaves), a cooperative launch of 2^lo CTAs: CTA k
+// runs node k >> (lo - l) of every level l whose node it is the leftmost
+// descendant of, waiting for the parent's ready flag (= epoch of this call).
+// The wait polls at most wait_limit times; on expiry the CTA records
+// HSS_ERR_TIMEOUT (with the level and node) in status and returns, and the
+// CTAs below it then give up the same way.
+template <typename T>
+__global__ void __launch_bounds__(NT)
+tree_bwd_kernel(TreeLevels<T> lv, int lo, int b, int c, int r, int nrhs, int* __restrict__ ready,
+                int epoch, long long wait_limit, int* status, int CB, int NBUF) {
+  __shared__ int ok;
+  const int k = blockIdx.x;
+  for (int l = 1; l <= lo; ++l) {
+    const int shift = lo - l;
+    if (k & ((1 << shift) - 1)) continue;   // another CTA runs this level's node
+    const int i = k >> shift;
+    if (l > 1) {
+      if (threadIdx.x == 0) {
+        const int* f = ready + (1 << (l - 1)) - 1 + (i >> 1);
+        int got = 0;
+        for (long long it = 0; it < wait_limit; ++it) {
+          if (ld_acquire(f) == epoch) {
+            got = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+        ok = got;
+      }
+      __syncthreads();
+      if (!ok) {
+        if (threadIdx.x == 0) report_failure(status, -6 /*TIMEOUT*/, l, i, -1);
+        return;
+      }
+    }
+    const int n = 1 << l;
+    bwd_node<T, true>(i, lv.M[l], b, (long long)b * b, b, c, lv.vec[l], n * b, b, nrhs,
+                      lv.vec[l - 1], (n / 2) * b, r, lv.V[l], (long long)b * r, lv.Tm[l],
+                      (long long)r * r, r, CB, NBUF);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(ready + (1 << l) - 1 + i, epoch);
   }
 }
 
@@ -1215,6 +1329,37 @@ cudaError_t launch_ulv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X
 }
 
 template <typename T>
+cudaError_t launch_tree_fwd(const TreeLevels<T>& lv, int lo, int b, int c, int r, int nrhs,
+                            int* cnt, cudaStream_t st) {
+  if (lo < 1 || lo > 20 || nrhs > 16 || r < 1 || r > NT || r > b) return cudaErrorInvalidValue;
+  int CB, NBUF;
+  size_t sm;
+  cudaError_t e = trsv_config<T>(tree_fwd_kernel<T>, b, nrhs, r, false, &CB, &NBUF, &sm);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(cnt, 0, sizeof(int) << lo, st);
+  if (e != cudaSuccess) return e;
+  tree_fwd_kernel<T><<<1 << lo, NT, sm, st>>>(lv, lo, b, c, r, nrhs, cnt, CB, NBUF);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tree_bwd(const TreeLevels<T>& lv, int lo, int b, int c, int r, int nrhs,
+                            int* ready, int epoch, long long wait_limit, int* status,
+                            cudaStream_t st) {
+  if (lo < 1 || lo > 20 || nrhs > 16 || r < 1 || r > NT || r > b) return cudaErrorInvalidValue;
+  int CB, NBUF;
+  size_t sm;
+  cudaError_t e = trsv_config<T>(tree_bwd_kernel<T>, b, nrhs, r, true, &CB, &NBUF, &sm);
+  if (e != cudaSuccess) return e;
+  // the CTAs wait on one another: a cooperative launch, which the runtime
+  // refuses unless all of them can be resident at once
+  TreeLevels<T> lvc = lv;
+  void* args[] = {&lvc, &lo, &b, &c, &r, &nrhs, &ready, &epoch, &wait_limit, &status, &CB, &NBUF};
+  return cudaLaunchCooperativeKernel((const void*)tree_bwd_kernel<T>, dim3(1u << lo), dim3(NT),
+                                     args, sm, st);
+}
+
+template <typename T>
 cudaError_t launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                             long long sX, int nrhs, T* Par, int ldpar, long long sPar, int nodes,
                             cudaStream_t st) {
@@ -1254,6 +1399,10 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
   template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int, int,\
                                             int*, int, bool, cudaStream_t);                       \
   template cudaError_t launch_scatter_ss<T>(const T*, int, long long, int, int, T*, int,           \
-                                            long long, int, cudaStream_t);
+                                            long long, int, cudaStream_t);                       \
+  template cudaError_t launch_tree_fwd<T>(const TreeLevels<T>&, int, int, int, int, int, int*,    \
+                                          cudaStream_t);                                         \
+  template cudaError_t launch_tree_bwd<T>(const TreeLevels<T>&, int, int, int, int, int, int*,    \
+                                          int, long long, int*, cudaStream_t);
 INST(double)
 INST(float)

@@ -63,3 +63,33 @@ cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, dou
 template <typename T>
 cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T* PA, int ldpa,
                               long long sPA, int nodes, cudaStream_t st);
+
+// Levels 1 .. lo of the solve as one launch per direction (block order b = 2r
+// at every level; index = level): factored blocks M (b x b per node), compact-WY
+// V (b x r) and T (r x r), level vectors (node segments of b rows, ld 2^l b;
+// vec[0] is the root's vector).
+template <typename T>
+struct TreeLevels {
+  const T* M[24];
+  const T* V[24];
+  const T* Tm[24];
+  T* vec[24];
+};
+
+// Forward sweep of levels lo .. 1 (Qᵀ, triangular solve, push to the parent)
+// in one launch of 2^lo CTAs with no barrier between levels: the CTA that
+// completes the second child of a parent continues with the parent.  cnt: 2^lo
+// ints of scratch (cleared here).  nrhs <= 16.
+template <typename T>
+cudaError_t launch_tree_fwd(const TreeLevels<T>& lv, int lo, int b, int c, int r, int nrhs,
+                            int* cnt, cudaStream_t st);
+
+// Backward sweep of levels 1 .. lo in one cooperative launch of 2^lo CTAs:
+// each node waits for its parent's flag in ready (2^(lo+1) ints, flag of node
+// i of level l at (2^l - 1) + i) to equal epoch, polling at most wait_limit
+// times; an expired wait records HSS_ERR_TIMEOUT in status.  Flags are left at
+// epoch, so every call passes a new one.
+template <typename T>
+cudaError_t launch_tree_bwd(const TreeLevels<T>& lv, int lo, int b, int c, int r, int nrhs,
+                            int* ready, int epoch, long long wait_limit, int* status,
+                            cudaStream_t st);

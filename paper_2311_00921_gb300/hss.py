@@ -33,11 +33,13 @@ class Shape(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("ir_max_it", ctypes.c_int32),
                 ("ir_tol", ctypes.c_double), ("residual", ctypes.c_int32),
-                ("basis", ctypes.c_int32), ("wait_budget", ctypes.c_int64)]
+                ("basis", ctypes.c_int32), ("wait_budget", ctypes.c_int64),
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 RESIDUALS = {"fp64": 0, "pair32": 1}
 BASIS_METHODS = {"auto": 0, "householder": 1}
+SCHEDULES = {"async": 0, "levels": 1}
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -168,14 +170,15 @@ class HSS:
             pass
 
     def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, residual="fp64",
-                  stream=None, wait_budget=0, basis="auto"):
+                  stream=None, wait_budget=0, basis="auto", schedule="async"):
         """residual: arithmetic of the refinement residual of the mixed modes,
         "fp64" or "pair32" (pairs of FP32 numbers, 48-bit significands).
         wait_budget: polls of a device-side pipeline wait (0 = default, < 0 =
         give up at once).  basis: "auto" (Cholesky QR + reconstruction) or
-        "householder" (the method of the basis completion)."""
+        "householder" (the method of the basis completion).  schedule: "async"
+        (upper solve levels as one launch per direction) or "levels"."""
         opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual],
-                      BASIS_METHODS[basis], wait_budget)
+                      BASIS_METHODS[basis], wait_budget, SCHEDULES[schedule], 0)
         _check(load().hss_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_factorize")
         self.precision = precision

@@ -462,3 +462,41 @@ def test_rank_above_the_per_node_limit():
         for i in range(2 ** l):
             check_close(q_from_vt(V[i], T[i]), F32.Q[l][i].astype(np.float64), 2e-4,
                         f"Q32 l={l} i={i}")
+
+
+# ---------------------------------------------------------------- schedule of the solve
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_async_and_level_schedules_agree(prec):
+    """Eight levels (so the tree launches cover levels 6 .. 1 and two level-by-level
+    levels sit below them): the asynchronous schedule of the upper solve levels
+    and the level-by-level one give the oracle's solution."""
+    h = I.random_hss(8, 32, 8, seed=8, orthonormal=False)
+    F = O.factor(h)
+    b = I.rhs(h.n, 16, 2)
+    x_ref = O.solve(F, b)
+    for sched in ("async", "levels"):
+        dev = hss.HSS(h)
+        dev.factorize(prec, schedule=sched)
+        x = dev.solve(hss.colmajor(b)).cpu().numpy()
+        err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+        assert err.max() <= 1e-10, (sched, err.max())
+
+
+def test_solve_wait_budget_runs_out():
+    """The backward sweep's ready-flag waits with a budget that gives up at once:
+    the solve reports HSS_ERR_TIMEOUT (with the level and node where the first
+    wait gave up) at the next synchronizing call, and a normal factorization and
+    solve of the same object afterwards are correct."""
+    h = I.random_hss(4, 32, 8, seed=44, orthonormal=False)
+    dev = hss.HSS(h)
+    dev.factorize("fp64", wait_budget=-1)
+    b = I.rhs(h.n, 2, 3)
+    dev.solve(hss.colmajor(b))
+    info = dev.last_info()
+    assert info["code"] == -6 and info["level"] >= 2, info
+    dev.factorize("fp64")
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    assert dev.last_info()["code"] == 0
+    x_ref = O.solve(O.factor(h), b)
+    err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    assert err.max() <= 1e-10, err
