@@ -93,15 +93,15 @@ typedef enum { HSS_RESIDUAL_FP64 = 0, HSS_RESIDUAL_PAIR32 = 1 } hss_residual;
 
 /* Method of the basis completion (Eq. 2-3); both give the same V, T and L_B up
  * to rounding (the Householder QL with LAPACK's dlarfg signs).
- * HSS_BASIS_AUTO: Cholesky QR twice of the reversed basis as level-wide
+ * HSS_BASIS_HOUSEHOLDER (default): the Householder kernel, one CTA per node
+ * with a CTA-wide reduction per column.
+ * HSS_BASIS_CHOLQR: Cholesky QR twice of the reversed basis as level-wide
  * products, then the Householder vectors reconstructed from the orthonormal
  * factor by an unpivoted LU of its top block (one CTA per node); nodes whose
  * Gram matrix is not numerically positive definite in the working precision,
  * and ranks too large for the per-node kernels (above 165 in FP64, 234 in
- * FP32), use the Householder kernel.
- * HSS_BASIS_HOUSEHOLDER: the Householder kernel (one CTA per node, a
- * CTA-wide reduction per column) for every node. */
-typedef enum { HSS_BASIS_AUTO = 0, HSS_BASIS_HOUSEHOLDER = 1 } hss_basis_method;
+ * FP32), use the Householder kernel. */
+typedef enum { HSS_BASIS_HOUSEHOLDER = 0, HSS_BASIS_CHOLQR = 1 } hss_basis_method;
 
 /* Schedule of the solve's upper levels (the levels of at most 64 nodes above
  * the leaves).  HSS_SCHEDULE_ASYNC: one launch per direction for all of them,

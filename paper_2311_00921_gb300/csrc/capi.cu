@@ -86,12 +86,14 @@ struct hss_s {
   int factorized = 0;
   int precision = HSS_FP64;
   int use_tc = 0;                      // tensor-core contractions in the FP32 factor
+  void* tc_ws = nullptr;               // packed tensor-core operands (allocated on first use)
+  size_t tc_ws_bytes = 0;
   TcMode tc_mode = TcMode::TF32x3;
   int ir_max_it = 30;
   double ir_tol = 1e-12;
   long long wait_budget = 0;           // polls of a device pipeline wait (0 = default)
   int residual = HSS_RESIDUAL_FP64;    // arithmetic of the refinement residual
-  int basis_method = HSS_BASIS_AUTO;   // method of the basis completion
+  int basis_method = HSS_BASIS_HOUSEHOLDER;   // method of the basis completion
   int schedule = HSS_SCHEDULE_ASYNC;   // launches of the solve's upper levels
   int* tree_cnt = nullptr;             // arrival counts of the tree forward sweep
   int* tree_ready = nullptr;           // ready flags of the tree backward sweep
@@ -392,7 +394,7 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
     const long long br = (long long)b * r;
     // (a) basis completion (Eq. 2-3)
     const T* Bsrc = (l == L) ? f.U : P.B;
-    if (h->basis_method == HSS_BASIS_AUTO && r <= basis_max_rank<T>()) {
+    if (h->basis_method == HSS_BASIS_CHOLQR && r <= basis_max_rank<T>()) {
       // Cholesky QR twice + Householder reconstruction; Householder kernel for
       // the nodes it flags
       BasisTrace bt{h, qs, sizeof(T) == 4};
@@ -447,8 +449,11 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
       if (h->use_tc) {
         tc = true;
         Launch k(h, HSS_K_TC_GEMM, 2.0 * b * r * (double)b * n, st);
-        if (tc_gemm(h->tc_mode, b, r, b, Ain, b, bb, P.V, b, br, /*b_ncontig=*/false, f.W, b, br,
-                    n, h->status, h->wait_budget, st) != cudaSuccess)
+        // W (b x r) = A V: rows of A against columns of V, both along K = b
+        const TcOperand a{Ain, b, bb, nullptr, 0, 0, 0, false};
+        const TcOperand v{P.V, b, br, nullptr, 0, 0, 0, true};
+        if (tc_gemm(h->tc_mode, b, r, b, a, v, f.W, b, br, n, h->tc_ws, h->tc_ws_bytes,
+                    h->status, h->wait_budget, st) != cudaSuccess)
           return HSS_ERR_CUDA;
       }
     }
@@ -462,7 +467,7 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
       if constexpr (std::is_same<T, float>::value) {
         Launch k(h, HSS_K_TC_SYR2K, 2.0 * r * b * (b + 1.0) * n, st);
         if (tc_syr2k_lower(h->tc_mode, b, r, Ain, b, bb, f.Y, b, br, P.V, b, br, P.M, b, bb, n,
-                           h->status, h->wait_budget, st) != cudaSuccess)
+                           h->tc_ws, h->tc_ws_bytes, h->status, h->wait_budget, st) != cudaSuccess)
           return HSS_ERR_CUDA;
       }
     } else {
@@ -1031,6 +1036,7 @@ void hss_destroy(hss_t h) {
   if (h->mstream) cudaStreamDestroy(h->mstream);
   cudaFree(h->arena);
   if (h->f32.arena) cudaFree(h->f32.arena);
+  if (h->tc_ws) cudaFree(h->tc_ws);
   cudaSetDevice(cur);
   delete h;
 }
@@ -1044,7 +1050,7 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
   if (opt && (opt->ir_max_it < 0 || !(opt->ir_tol >= 0.0))) return HSS_ERR_INVALID_ARG;
   if (opt && opt->residual != HSS_RESIDUAL_FP64 && opt->residual != HSS_RESIDUAL_PAIR32)
     return HSS_ERR_INVALID_ARG;
-  if (opt && opt->basis != HSS_BASIS_AUTO && opt->basis != HSS_BASIS_HOUSEHOLDER)
+  if (opt && opt->basis != HSS_BASIS_HOUSEHOLDER && opt->basis != HSS_BASIS_CHOLQR)
     return HSS_ERR_INVALID_ARG;
   if (opt && opt->schedule != HSS_SCHEDULE_ASYNC && opt->schedule != HSS_SCHEDULE_LEVELS)
     return HSS_ERR_INVALID_ARG;
@@ -1063,11 +1069,29 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     h->schedule = opt->schedule;
   } else {
     h->wait_budget = 0;
-    h->basis_method = HSS_BASIS_AUTO;
+    h->basis_method = HSS_BASIS_HOUSEHOLDER;
     h->schedule = HSS_SCHEDULE_ASYNC;
   }
   h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
   h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;
+  if (h->use_tc) {   // packing workspace of the largest level's contractions
+    size_t need = 0;
+    for (int l = h->L; l >= 1; --l) {
+      const int b = (l == h->L) ? h->leaf : 2 * h->rank, n = 1 << l;
+      need = std::max(need, tc_workspace_bytes(h->tc_mode, b, h->rank, b, n));
+      need = std::max(need, tc_workspace_bytes(h->tc_mode, b, b, 2 * h->rank, n));
+    }
+    if (need > h->tc_ws_bytes) {
+      if (h->tc_ws) cudaFree(h->tc_ws);
+      h->tc_ws = nullptr;
+      h->tc_ws_bytes = 0;
+      if (cudaMalloc(&h->tc_ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return HSS_ERR_OOM;
+      }
+      h->tc_ws_bytes = need;
+    }
+  }
   int rc = factorize(h, prec, st);
   if (rc) return rc;
   h->precision = prec;

@@ -2,23 +2,27 @@
 // diagonal product in the mixed-precision factorization (Alg. 2, in the
 // compact-WY form): W = A V and the rank-2r update A - Y'Vᵀ - V Y'ᵀ.
 //
-// One CTA (4 warps) owns a 128 x 128 output tile; the accumulator lives in
-// tensor memory (128 lanes x 128 FP32 columns).  The threads stage 128 x 32
-// slabs of the FP32 operands into shared memory in the canonical K-major,
-// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix; K-adjacent
-// core matrices 128 B apart, 8-row groups 1 KB apart), converting them to the
-// MMA input type on the way (TF32 or BF16, optionally split into hi + lo so
-// that hi·hi + hi·lo + lo·hi keeps the product close to FP32 accuracy).  One
-// thread issues tcgen05.mma; tcgen05.commit arrives on the stage's mbarrier
-// when the MMAs that read it are done, which gates the refill of that stage
-// (two stages).  The epilogue reads the tile with tcgen05.ld (each warp its 32
-// TMEM lanes) and writes alpha·acc + beta·C_in, optionally only on and below
-// the diagonal.  Every mbarrier wait is bounded: on expiry the kernel records
-// HSS_ERR_TIMEOUT in the status word, stops issuing, waits (bounded) for the
-// MMAs already issued, frees its tensor memory and returns.  The pipeline
-// waits poll at most `wait_limit` times (set by the caller; 0 polls = give up
-// at once); the final wait for issued MMAs always uses the long default, so
-// that tensor memory is never released under a pending MMA.
+// Operands are packed once per level (tc_pack_kernel) into slabs of 128 rows x
+// 32 K elements in the canonical K-major, no-swizzle core-matrix layout of the
+// MMA (8 rows x 16 bytes per core matrix; K-adjacent core matrices 128 B apart,
+// 8-row groups one K-row of core matrices apart), converted to the MMA input
+// type and, in the x3 modes, split into hi + lo parts (hi·hi + hi·lo + lo·hi
+// is accumulated).  The GEMM kernel (one CTA of 4 warps per 128 x 128 output
+// tile, FP32 accumulator in tensor memory) streams the slabs through a ring of
+// shared-memory stages with cp.async.bulk (the TMA engine, completion counted
+// in bytes on each stage's "full" mbarrier); one thread issues the copies and
+// the tcgen05.mma instructions, whose tcgen05.commit arrives on the stage's
+// "empty" mbarrier that gates its refill.  The refill of a stage waits for the
+// MMAs of the previous slab, so one slab of MMAs is always queued behind the
+// ones executing.  The epilogue reads the tile with tcgen05.ld (each warp its
+// 32 TMEM lanes) and writes alpha·acc + beta·C_in, optionally only on and below
+// the diagonal.
+//
+// Every wait is bounded.  The ring's waits poll at most `wait_limit` times (set
+// by the caller; 0 polls = give up at once): on expiry the kernel records
+// HSS_ERR_TIMEOUT in the status word, stops issuing, waits with the long
+// default for the copies and MMAs it has issued, frees its tensor memory and
+// returns without writing the tile.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -33,6 +37,7 @@ constexpr int TM = 128, TN = 128, TK = 32;   // CTA tile and K slab (elements)
 constexpr int TC_THREADS = 128;
 constexpr uint32_t kTmemCols = 128;
 constexpr long long kWaitLimit = 1LL << 24;   // default polls before a wait gives up
+constexpr int kSmemBudget = 200 * 1024;       // dynamic shared memory of the ring
 
 HSS_DEVINL uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -68,6 +73,24 @@ HSS_DEVINL bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
   return false;
 }
 
+HSS_DEVINL void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+HSS_DEVINL void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
+// global -> shared bulk copy on the TMA engine; completes `bytes` on mbar
+HSS_DEVINL void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
 template <typename E>
 struct TcType;
 template <>
@@ -89,66 +112,93 @@ struct TcType<__nv_bfloat16> {
   HSS_DEVINL static __nv_bfloat16 conv(float x) { return __float2bfloat16_rn(x); }
 };
 
-// byte offset of element (row, k) of a 128 x TK slab in the core-matrix layout
 template <typename E>
-HSS_DEVINL uint32_t slab_offset(int row, int k) {
-  constexpr int epc = 16 / sizeof(E);                  // elements per 16-byte core row
-  constexpr uint32_t kcores = TK / epc;                // core matrices along K
-  return ((uint32_t)(row >> 3) * kcores + (uint32_t)(k / epc)) * 128u + (uint32_t)(row & 7) * 16u +
-         (uint32_t)(k % epc) * (uint32_t)sizeof(E);
+constexpr uint32_t slab_bytes() {
+  return (uint32_t)(TM * TK * sizeof(E));
 }
 
-// Stage rows [r0, r0+128) x k [k0, k0+TK) of an operand into the slab(s).
-// mcontig: element (row, k) at X[row + k * ld]; otherwise at X[k + row * ld].
-template <typename E, int NPASS>
-HSS_DEVINL void stage(const float* X, int ld, bool mcontig, int rows_valid, int r0, int kvalid,
-                      int k0, unsigned char* hi_slab, unsigned char* lo_slab) {
+// Pack rows [rb 128, rb 128 + 128) x K [kb 32, kb 32 + 32) of an operand into
+// one slab (and its lo slab right after it), core-matrix order.  The operand's
+// element (row, k) is, for k < K1, src1[k + row ld1] (kcontig) or
+// src1[row + k ld1], else the same in src2 with k - K1; zero outside rows x K.
+// Packed layout per node: [row block][K block][part][slab].  One CTA per slab.
+template <typename E, int NPARTS>
+__global__ void __launch_bounds__(256)
+tc_pack_kernel(const float* __restrict__ s1, int ld1, long long ss1, const float* __restrict__ s2,
+               int ld2, long long ss2, int K1, int K, int kcontig, int rows, int nkb,
+               unsigned char* __restrict__ out, long long s_out) {
+  __shared__ float t[TM][TK + 1];
+  const long long node = blockIdx.y;
+  const int rb = blockIdx.x / nkb, kb = blockIdx.x % nkb;
+  const int r0 = rb * TM, k0 = kb * TK;
   const int tid = threadIdx.x;
-  for (int e = tid; e < TM * TK; e += TC_THREADS) {
-    int row, k;
-    if (mcontig) { row = e % TM; k = e / TM; } else { k = e % TK; row = e / TK; }
-    const int gr = r0 + row, gk = k0 + k;
+  for (int e = tid; e < TM * TK; e += 256) {
+    int row, kk;
+    if (kcontig) {
+      kk = e % TK;
+      row = e / TK;
+    } else {
+      row = e % TM;
+      kk = e / TM;
+    }
+    const int gr = r0 + row, gk = k0 + kk;
     float v = 0.f;
-    if (gr < rows_valid && gk < kvalid) v = mcontig ? X[gr + (long long)gk * ld] : X[gk + (long long)gr * ld];
-    const uint32_t off = slab_offset<E>(row, k);
+    if (gr < rows && gk < K) {
+      const bool first = gk < K1;
+      const float* s = first ? s1 + node * ss1 : s2 + node * ss2;
+      const int ld = first ? ld1 : ld2;
+      const int k = first ? gk : gk - K1;
+      v = kcontig ? s[k + (long long)gr * ld] : s[gr + (long long)k * ld];
+    }
+    t[row][kk] = v;
+  }
+  __syncthreads();
+  constexpr int epc = 16 / sizeof(E);   // elements per 16-byte core row
+  constexpr int kcores = TK / epc;      // core matrices along K
+  E* hi = reinterpret_cast<E*>(out + node * s_out +
+                               (size_t)blockIdx.x * NPARTS * slab_bytes<E>());
+  E* lo = hi + TM * TK;
+  for (int o = tid; o < TM * TK; o += 256) {
+    const int core = o / (8 * epc), within = o % (8 * epc);
+    const int row = (core / kcores) * 8 + within / epc;
+    const int kk = (core % kcores) * epc + within % epc;
+    const float v = t[row][kk];
     const float h = TcType<E>::hi(v);
-    *reinterpret_cast<E*>(hi_slab + off) = TcType<E>::conv(h);
-    if (NPASS == 3) *reinterpret_cast<E*>(lo_slab + off) = TcType<E>::conv(v - h);
+    hi[o] = TcType<E>::conv(h);
+    if (NPARTS == 2) lo[o] = TcType<E>::conv(v - h);
   }
 }
 
-struct Term {
-  const float* A;
-  int lda;
-  long long sA;
-  bool a_mcontig;
-  const float* B;
-  int ldb;
-  long long sB;
-  bool b_ncontig;   // element (n, k) of B at B[n + k * ldb] (else at B[k + n * ldb])
-  int K;
-};
+}  // namespace
 
+namespace {
+
+// C (M x N) tile (tm, tn) of node blockIdx.y = Σ over nk K slabs of A_slab · B_slabᵀ
+// (packed operands, see tc_pack_kernel; A has tiles_m row blocks, B the N ones).
 template <typename E, int NPASS>
 __global__ void __launch_bounds__(TC_THREADS)
-tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const float* Cin,
-               int ldcin, long long sCin, float* C, int ldc, long long sC, int lower_only,
-               int tiles_m, int* status, long long wait_limit) {
-  constexpr int NSLAB = (NPASS == 3) ? 4 : 2;                  // A hi/lo, B hi/lo
-  constexpr uint32_t SLAB = TM * TK * sizeof(E);               // bytes per slab
-  constexpr uint32_t STAGE = NSLAB * SLAB;
+tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long long sAp,
+               const unsigned char* __restrict__ Bp, long long sBp, float alpha, float beta,
+               const float* Cin, int ldcin, long long sCin, float* C, int ldc, long long sC,
+               int lower_only, int tiles_m, int stages, int* status, long long wait_limit) {
+  constexpr int NPARTS = (NPASS == 3) ? 2 : 1;
+  constexpr uint32_t SLAB = slab_bytes<E>();
+  constexpr uint32_t OPER = NPARTS * SLAB;    // one operand's slab(s) of a stage
+  constexpr uint32_t STAGE = 2 * OPER;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[8], empty[8], done;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const long long bz = blockIdx.z;
-  // tile coordinates (lower_only: enumerate tile pairs tm >= tn)
+  const long long bz = blockIdx.y;
   int tm, tn;
-  if (lower_only) {
+  if (lower_only) {   // tile pairs tm >= tn
     int t = blockIdx.x, ti = 0;
-    while (t > ti) { t -= ti + 1; ++ti; }
+    while (t > ti) {
+      t -= ti + 1;
+      ++ti;
+    }
     tm = ti;
     tn = t;
   } else {
@@ -156,15 +206,22 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
     tn = blockIdx.x / tiles_m;
   }
   const int m0 = tm * TM, n0 = tn * TN;
+  const unsigned char* a_src = Ap + bz * sAp + (size_t)tm * nk * OPER;
+  const unsigned char* b_src = Bp + bz * sBp + (size_t)tn * nk * OPER;
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base_s)), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(kTmemCols)
+                 : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[0])), "r"(1) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar[1])), "r"(1) : "memory");
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(&done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
   }
@@ -173,38 +230,39 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_s;
 
-  const int k1s = (t1.K + TK - 1) / TK, k2s = (t2.K + TK - 1) / TK;
-  const int nk = k1s + k2s;
-  const uint32_t idesc = make_idesc(TcType<E>::fmt, TM, TN);
-  int issued = 0;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int s = kc & 1;
-    unsigned char* st = smem + s * STAGE;
-    if (kc >= 2) {   // the MMAs that read this stage two slabs ago are done
-      if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((kc >> 1) - 1) & 1), wait_limit))
-        abort_s = 1;
-      __syncthreads();
-      if (abort_s) break;
-    }
-    const Term& t = (kc < k1s) ? t1 : t2;
-    const int k0 = ((kc < k1s) ? kc : kc - k1s) * TK;
-    stage<E, NPASS>(t.A + bz * t.sA, t.lda, t.a_mcontig, M, m0, t.K, k0, st,
-                    st + 2 * SLAB);
-    stage<E, NPASS>(t.B + bz * t.sB, t.ldb, t.b_ncontig, N, n0, t.K, k0, st + SLAB,
-                    st + 3 * SLAB);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  if (tid == 0) {
+    const uint32_t sbase = smem_u32(smem);
+    auto load = [&](int kc) {   // slab kc into stage kc % stages
+      const int s = kc % stages;
+      const uint32_t dst = sbase + s * STAGE, fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, STAGE);
+      bulk_g2s(dst, a_src + (size_t)kc * OPER, OPER, fb);
+      bulk_g2s(dst + OPER, b_src + (size_t)kc * OPER, OPER, fb);
+    };
+    const uint32_t idesc = make_idesc(TcType<E>::fmt, TM, TN);
+    constexpr int kpi = TcType<E>::kpi;
+    constexpr uint32_t step = (uint32_t)(kpi * sizeof(E) / 16) * 128u;   // bytes per MMA K-step
+    constexpr uint32_t sbo = (uint32_t)(TK * sizeof(E) / 16) * 128u;     // 8-row group pitch
+    int loaded = 0;   // slabs whose copies have been issued
+    for (; loaded < nk && loaded < stages; ++loaded) load(loaded);
+    int waited = 0;   // slabs whose copies have landed (full waits passed)
+    int abort = 0;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % stages;
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((kc / stages) & 1), wait_limit)) {
+        abort = 1;
+        break;
+      }
+      waited = kc + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + SLAB);
-      const uint32_t a_lo = smem_u32(st + 2 * SLAB), b_lo = smem_u32(st + 3 * SLAB);
-      constexpr int kpi = TcType<E>::kpi;
-      constexpr uint32_t step = (uint32_t)(kpi * sizeof(E) / 16) * 128u;   // bytes per MMA K-step
-      constexpr uint32_t sbo = (uint32_t)(TK * sizeof(E) / 16) * 128u;     // 8-row group pitch
+      const uint32_t a_hi = sbase + s * STAGE, b_hi = a_hi + OPER;
+      const uint32_t a_lo = a_hi + SLAB, b_lo = b_hi + SLAB;
+#pragma unroll
       for (int ks = 0; ks < TK / kpi; ++ks) {
         const uint32_t o = ks * step;
         const uint32_t pa[3] = {a_hi, a_hi, a_lo};
         const uint32_t pb[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
         for (int p = 0; p < NPASS; ++p) {
           const uint64_t ad = make_desc(pa[p] + o, 128, sbo);
           const uint64_t bd = make_desc(pb[p] + o, 128, sbo);
@@ -212,25 +270,43 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
           if (TcType<E>::fmt == 2)
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
           else
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&mbar[s])) : "memory");
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&empty[s]))
+          : "memory");
+      // refill the stage of the previous slab once its MMAs are done
+      if (kc >= 1 && loaded < nk) {
+        const int sp = (kc - 1) % stages;
+        if (!mbar_wait(smem_u32(&empty[sp]), (uint32_t)(((kc - 1) / stages) & 1), wait_limit)) {
+          abort = 1;
+          break;
+        }
+        load(loaded++);
+      }
     }
-    issued = kc + 1;
-  }
-  // wait for every issued MMA (commit tracks all earlier MMAs of the thread)
-  if (tid == 0 && issued > 0) {
-    const int last = issued - 1;
-    if (!mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), kWaitLimit))
-      abort_s = 2;
+    if (abort) {
+      // copies still in flight land before the CTA may exit
+      for (int kc = waited; kc < loaded; ++kc)
+        mbar_wait(smem_u32(&full[kc % stages]), (uint32_t)((kc / stages) & 1), kWaitLimit);
+      abort_s = 1;
+    }
+    // every MMA issued so far completes before `done` arrives
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&done))
+        : "memory");
+    if (!mbar_wait(smem_u32(&done), 0u, kWaitLimit)) abort_s = 2;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -242,6 +318,7 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
     const float* cin = Cin ? Cin + bz * sCin : nullptr;
     float* c = C + bz * sC;
     for (int c0 = 0; c0 < TN; c0 += 32) {
+      if (n0 + c0 >= N) break;
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
       asm volatile(
@@ -272,65 +349,119 @@ tc_gemm_kernel(int M, int N, Term t1, Term t2, float alpha, float beta, const fl
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
                  : "memory");
-}
-
-template <typename E, int NPASS>
-cudaError_t launch(int M, int N, const Term& t1, const Term& t2, float alpha, float beta,
-                   const float* Cin, int ldcin, long long sCin, float* C, int ldc, long long sC,
-                   bool lower, int batch, int* status, long long wait_limit, cudaStream_t st) {
-  constexpr int NSLAB = (NPASS == 3) ? 4 : 2;
-  // at least 57 KB so that no more than 4 CTAs (4 x 128 TMEM columns) share an SM
-  const size_t smem = std::max<size_t>(2 * (size_t)NSLAB * TM * TK * sizeof(E), 57 * 1024);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(tc_gemm_kernel<E, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return cudaErrorInvalidConfiguration;
-    attr = true;
-  }
-  const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
-  const int tiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
-  dim3 g(tiles, 1, batch);
-  tc_gemm_kernel<E, NPASS><<<g, TC_THREADS, smem, st>>>(M, N, t1, t2, alpha, beta, Cin, ldcin, sCin,
-                                                       C, ldc, sC, lower ? 1 : 0, tiles_m, status,
-                                                       wait_limit);
-  return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t tc_gemm(TcMode mode, int M, int N, int K, const float* A, int lda, long long sA,
-                    const float* B, int ldb, long long sB, bool b_ncontig, float* C, int ldc,
-                    long long sC, int batch, int* status, long long wait_budget,
-                    cudaStream_t st) {
-  const long long wl = wait_budget > 0 ? wait_budget : (wait_budget < 0 ? 0 : kWaitLimit);
-  Term t1{A, lda, sA, true, B, ldb, sB, b_ncontig, K};
-  Term t2{A, lda, sA, true, B, ldb, sB, b_ncontig, 0};
-  switch (mode) {
-    case TcMode::TF32: return launch<float, 1>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
-    case TcMode::TF32x3: return launch<float, 3>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
-    case TcMode::BF16: return launch<__nv_bfloat16, 1>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
-    case TcMode::BF16x3: return launch<__nv_bfloat16, 3>(M, N, t1, t2, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, status, wl, st);
+namespace {
+
+template <typename E, int NPASS>
+size_t packed_bytes(int rows, int K, int batch) {
+  constexpr int NPARTS = (NPASS == 3) ? 2 : 1;
+  const size_t slabs = (size_t)((rows + TM - 1) / TM) * ((K + TK - 1) / TK);
+  return slabs * NPARTS * slab_bytes<E>() * (size_t)batch;
+}
+
+template <typename E, int NPASS>
+void pack(const TcOperand& x, int rows, int K, int batch, unsigned char* out, cudaStream_t st) {
+  constexpr int NPARTS = (NPASS == 3) ? 2 : 1;
+  const int nkb = (K + TK - 1) / TK, nrb = (rows + TM - 1) / TM;
+  const long long s_out = (long long)nrb * nkb * NPARTS * slab_bytes<E>();
+  const float* s2 = x.src2 ? x.src2 : x.src1;
+  tc_pack_kernel<E, NPARTS><<<dim3(nrb * nkb, batch), 256, 0, st>>>(
+      x.src1, x.ld1, x.s1, s2, x.src2 ? x.ld2 : x.ld1, x.src2 ? x.s2 : x.s1, x.K1 ? x.K1 : K, K,
+      x.kcontig ? 1 : 0, rows, nkb, out, s_out);
+}
+
+template <typename E, int NPASS>
+cudaError_t run(int M, int N, int K, const TcOperand& a, const TcOperand& b, float alpha,
+                float beta, const float* Cin, int ldcin, long long sCin, float* C, int ldc,
+                long long sC, bool lower, int batch, void* ws, size_t ws_bytes, int* status,
+                long long wait_limit, cudaStream_t st) {
+  constexpr int NPARTS = (NPASS == 3) ? 2 : 1;
+  constexpr uint32_t STAGE = 2 * NPARTS * slab_bytes<E>();
+  const size_t pa = packed_bytes<E, NPASS>(M, K, batch), pb = packed_bytes<E, NPASS>(N, K, batch);
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
+  if (pa + pb > ws_bytes || batch > 65535) return cudaErrorInvalidValue;
+  unsigned char* Ap = static_cast<unsigned char*>(ws);
+  unsigned char* Bp = Ap + pa;
+  pack<E, NPASS>(a, M, K, batch, Ap, st);
+  pack<E, NPASS>(b, N, K, batch, Bp, st);
+  const int stages = std::min<int>(8, kSmemBudget / STAGE);
+  const size_t smem = (size_t)stages * STAGE;
+  static size_t attr = 0;
+  if (smem > attr) {
+    if (cudaFuncSetAttribute(tc_gemm_kernel<E, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return cudaErrorInvalidConfiguration;
+    attr = smem;
   }
+  const int nk = (K + TK - 1) / TK;
+  const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
+  const int tiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
+  tc_gemm_kernel<E, NPASS><<<dim3(tiles, batch), TC_THREADS, smem, st>>>(
+      M, N, nk, Ap, (long long)(pa / batch), Bp, (long long)(pb / batch), alpha, beta, Cin, ldcin,
+      sCin, C, ldc, sC, lower ? 1 : 0, tiles_m, stages, status, wait_limit);
+  return cudaGetLastError();
+}
+
+long long wait_limit_of(long long budget) {
+  return budget > 0 ? budget : (budget < 0 ? 0 : kWaitLimit);
+}
+
+}  // namespace
+
+size_t tc_workspace_bytes(TcMode mode, int M, int N, int K, int batch) {
+  switch (mode) {
+    case TcMode::TF32: return packed_bytes<float, 1>(M, K, batch) + packed_bytes<float, 1>(N, K, batch);
+    case TcMode::TF32x3: return packed_bytes<float, 3>(M, K, batch) + packed_bytes<float, 3>(N, K, batch);
+    case TcMode::BF16:
+      return packed_bytes<__nv_bfloat16, 1>(M, K, batch) + packed_bytes<__nv_bfloat16, 1>(N, K, batch);
+    case TcMode::BF16x3:
+      return packed_bytes<__nv_bfloat16, 3>(M, K, batch) + packed_bytes<__nv_bfloat16, 3>(N, K, batch);
+  }
+  return 0;
+}
+
+cudaError_t tc_gemm(TcMode mode, int M, int N, int K, const TcOperand& a, const TcOperand& b,
+                    float* C, int ldc, long long sC, int batch, void* ws, size_t ws_bytes,
+                    int* status, long long wait_budget, cudaStream_t st) {
+  const long long wl = wait_limit_of(wait_budget);
+#define TC_RUN(E, NP)                                                                           \
+  run<E, NP>(M, N, K, a, b, 1.f, 0.f, nullptr, 0, 0, C, ldc, sC, false, batch, ws, ws_bytes, \
+             status, wl, st)
+  switch (mode) {
+    case TcMode::TF32: return TC_RUN(float, 1);
+    case TcMode::TF32x3: return TC_RUN(float, 3);
+    case TcMode::BF16: return TC_RUN(__nv_bfloat16, 1);
+    case TcMode::BF16x3: return TC_RUN(__nv_bfloat16, 3);
+  }
+#undef TC_RUN
   return cudaErrorInvalidValue;
 }
 
 cudaError_t tc_syr2k_lower(TcMode mode, int m, int k, const float* A, int lda, long long sA,
                            const float* P, int ldp, long long sP, const float* Q, int ldq,
-                           long long sQ, float* Mout, int ldm, long long sM, int batch, int* status,
-                           long long wait_budget, cudaStream_t st) {
-  const long long wl = wait_budget > 0 ? wait_budget : (wait_budget < 0 ? 0 : kWaitLimit);
-  // Mout = A - (P Qᵀ + Q Pᵀ) on and below the diagonal: two terms along K,
-  // operand A = P then Q (row-contiguous), operand B(n, k) = Q(n, k) then P(n, k)
-  Term t1{P, ldp, sP, true, Q, ldq, sQ, true, k};
-  Term t2{Q, ldq, sQ, true, P, ldp, sP, true, k};
+                           long long sQ, float* Mout, int ldm, long long sM, int batch, void* ws,
+                           size_t ws_bytes, int* status, long long wait_budget,
+                           cudaStream_t st) {
+  // Mout = A - [P Q] [Q P]ᵀ on and below the diagonal: K = 2k, the left operand
+  // row i = [P(i, :) Q(i, :)], the right one row j = [Q(j, :) P(j, :)]
+  const TcOperand a{P, ldp, sP, Q, ldq, sQ, k, false};
+  const TcOperand b{Q, ldq, sQ, P, ldp, sP, k, false};
+  const long long wl = wait_limit_of(wait_budget);
+#define TC_RUN(E, NP)                                                                           \
+  run<E, NP>(m, m, 2 * k, a, b, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, ws, ws_bytes, \
+             status, wl, st)
   switch (mode) {
-    case TcMode::TF32: return launch<float, 1>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
-    case TcMode::TF32x3: return launch<float, 3>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
-    case TcMode::BF16: return launch<__nv_bfloat16, 1>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
-    case TcMode::BF16x3: return launch<__nv_bfloat16, 3>(m, m, t1, t2, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, status, wl, st);
+    case TcMode::TF32: return TC_RUN(float, 1);
+    case TcMode::TF32x3: return TC_RUN(float, 3);
+    case TcMode::BF16: return TC_RUN(__nv_bfloat16, 1);
+    case TcMode::BF16x3: return TC_RUN(__nv_bfloat16, 3);
   }
+#undef TC_RUN
   return cudaErrorInvalidValue;
 }

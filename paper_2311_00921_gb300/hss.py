@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
 
 
 RESIDUALS = {"fp64": 0, "pair32": 1}
-BASIS_METHODS = {"auto": 0, "householder": 1}
+BASIS_METHODS = {"householder": 0, "cholqr": 1}
 SCHEDULES = {"async": 0, "levels": 1}
 
 
@@ -170,12 +170,12 @@ class HSS:
             pass
 
     def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, residual="fp64",
-                  stream=None, wait_budget=0, basis="auto", schedule="async"):
+                  stream=None, wait_budget=0, basis="householder", schedule="async"):
         """residual: arithmetic of the refinement residual of the mixed modes,
         "fp64" or "pair32" (pairs of FP32 numbers, 48-bit significands).
         wait_budget: polls of a device-side pipeline wait (0 = default, < 0 =
-        give up at once).  basis: "auto" (Cholesky QR + reconstruction) or
-        "householder" (the method of the basis completion).  schedule: "async"
+        give up at once).  basis: "householder" or "cholqr" (Cholesky QR +
+        Householder reconstruction; the method of the basis completion).  schedule: "async"
         (upper solve levels as one launch per direction) or "levels"."""
         opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual],
                       BASIS_METHODS[basis], wait_budget, SCHEDULES[schedule], 0)

@@ -405,13 +405,15 @@ def test_grid_exp_full_size_against_oracle():
 
 
 # ---------------------------------------------------------------- basis completion methods
-@pytest.mark.parametrize("levels,leaf,rank", [(3, 100, 13), (2, 256, 64)])
-def test_householder_basis_method(levels, leaf, rank):
-    """The Householder kernel (hss_options.basis = HOUSEHOLDER) per step and end
-    to end against the oracle, like the default method."""
+@pytest.mark.parametrize("levels,leaf,rank", [(3, 100, 13), (2, 256, 64), (4, 96, 40),
+                                               (2, 32, 32), (1, 64, 16)])
+def test_cholqr_basis_method(levels, leaf, rank):
+    """Cholesky QR + Householder reconstruction (hss_options.basis = CHOLQR) per
+    step and end to end against the oracle, like the default method; square
+    bases (rank = leaf) and one level included."""
     h = I.random_hss(levels, leaf, rank, seed=levels * 13 + leaf, orthonormal=False)
     dev = hss.HSS(h)
-    dev.factorize("fp64", basis="householder")
+    dev.factorize("fp64", basis="cholqr")
     F = O.factor(h)
     b = I.rhs(h.n, 3, 7)
     x = dev.solve(hss.colmajor(b)).cpu().numpy()
@@ -429,7 +431,7 @@ def test_ill_conditioned_basis_falls_back_to_householder(prec):
     rng = np.random.default_rng(5)
     h.U[5][:, 1] = h.U[5][:, 0] * (1.0 + 1e-9) + 1e-9 * rng.standard_normal(64)
     auto, ref = hss.HSS(h), hss.HSS(h)
-    auto.factorize(prec)
+    auto.factorize(prec, basis="cholqr")
     ref.factorize(prec, basis="householder")
     auto.sync()
     ref.sync()
@@ -447,14 +449,19 @@ def test_ill_conditioned_basis_falls_back_to_householder(prec):
 
 
 def test_rank_above_the_per_node_limit():
-    """Rank 176 (block order 352 above the leaves): FP64 completes the bases with
-    the Householder kernel (the reconstruction's r x r block exceeds shared
-    memory), FP32 with the reconstruction; both per step against the oracle."""
+    """Rank 176 (block order 352 above the leaves) with the Cholesky QR method:
+    FP64 completes the bases with the Householder kernel (the reconstruction's
+    r x r block exceeds shared memory), FP32 with the reconstruction; both per
+    step against the oracle."""
     h = I.random_hss(2, 256, 176, seed=176, orthonormal=False)
-    dev, F, b, x = run_both(h, 2)
+    dev = hss.HSS(h)
+    dev.factorize("fp64", basis="cholqr")
+    F = O.factor(h)
+    b = I.rhs(h.n, 2, 7)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
     check_steps(dev, F, h)
     check_end_to_end(dev, F, b, x)
-    dev.factorize("fp32")
+    dev.factorize("fp32", basis="cholqr")
     dev.sync()
     F32 = O.factor(h, dtype=np.float32)
     for l in range(h.levels, 0, -1):
