@@ -75,10 +75,26 @@ typedef enum {
 } hss_precision;
 
 typedef struct {
-  int32_t n;      /* matrix order, = leaf * 2^levels */
-  int32_t leaf;   /* leaf block order (1 .. 768; FP64 solves: see hss_solve) */
-  int32_t rank;   /* rank of every basis (1 .. min(leaf, 256)) */
+  int32_t n;      /* matrix order: leaf * 2^levels, or the sum of node_sizes */
+  int32_t leaf;   /* leaf block order (1 .. 768; FP64 solves: see hss_solve); with
+                     node_sizes, the largest leaf order */
+  int32_t rank;   /* rank of every basis (1 .. min(leaf, 256)); with node_sizes the
+                     largest rank, see below */
   int32_t levels; /* L >= 1 */
+  const int32_t* node_sizes; /* NULL: uniform tree.  Otherwise a host array of the
+                     2^levels leaf orders b_i (1 .. leaf, summing to n): an uneven
+                     tree, e.g. from median bisection of n points with n a multiple
+                     of nothing.  Ranks follow the orders: r_i = min(rank, b_i) at
+                     leaf i, r_p = min(rank, r_c1 + r_c2) at a parent of c1, c2.  The
+                     generators are then packed block after block with those
+                     shapes: D_i b_i x b_i, U_i b_i x r_i, E_{l;p} (r_c1 + r_c2) x r_p,
+                     S_{l;k} r_{2k+1} x r_{2k}.  The library embeds the tree in the
+                     uniform (leaf, rank) format -- identity on the padded diagonal,
+                     identity columns on the padded basis directions, zero padded
+                     couplings -- which is the matrix A ⊕ I up to a row
+                     permutation, so x and log det are those of A; vectors stay
+                     n x nrhs in cluster order (the library scatters and gathers
+                     them), hss_export returns the padded blocks. */
 } hss_shape;
 
 /* Arithmetic of the refinement residual r = b - A x of the mixed modes.
@@ -133,7 +149,8 @@ typedef struct {
 
 /* Create a device-resident HSS object from its generators (format above).
  * D, U, E, S are host pointers (on_device = 0) or device pointers of the current
- * device (on_device = 1); they are copied and the caller keeps ownership.  The
+ * device (on_device = 1; uniform trees only); they are copied and the caller
+ * keeps ownership.  The
  * object owns one device arena (inputs, factor, workspace for up to 32
  * right-hand-side columns per pass); it is tied to the device current at
  * creation.  E may be NULL when levels = 1.  Synchronous (returns after the
@@ -213,6 +230,7 @@ int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t l
  * shares the one array and overwrites all of the part it reads, so no state
  * carries over between calls -- but two calls that overlap on the GPU (other
  * streams, other host threads) race on it: serialize them.
+ * Uniform trees only (shape->node_sizes must be NULL).
  * Asynchronous on `stream`.  Errors: INVALID_ARG, TOO_LARGE, CUDA. */
 int hss_matvec_noalloc(const hss_shape* shape, const double* D, const double* U, const double* E,
                        const double* S, const double* x, double* y, int32_t nrhs, int32_t ld,

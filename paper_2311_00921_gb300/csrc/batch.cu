@@ -23,6 +23,7 @@
 #include "../../include/hss.h"
 #include "common.cuh"
 #include "ulv_kernels.cuh"
+#include "uneven.cuh"
 
 namespace {
 
@@ -67,6 +68,11 @@ struct hss_batch_s {
   int* status = nullptr;
   const double** ptr_tab = nullptr;   // device pointer table for gather / scatter
   long long* ptr_rows = nullptr;      // device: (rows, row offset) per matrix, then group lds
+  // uneven members: device row maps (padded row -> caller's row or -1), a table of
+  // them (null for uniform members) and the callers' orders
+  void* map_mem = nullptr;
+  const int** map_tab = nullptr;
+  long long* user_n = nullptr;
   void* arena = nullptr;
   int factorized = 0;
   cudaEvent_t ev_join = nullptr;
@@ -308,21 +314,29 @@ int solve_group(Group& g, int nc) {
   return HSS_OK;
 }
 
-// one CTA per matrix: copy n_i x nc between the matrix's own column-major
-// buffer (ld n_i) and its rows of its group's leaf vector
+// one CTA per matrix: copy nc columns between the matrix's own column-major
+// buffer (ld = its order) and its rows (n_i of the uniform tree) of its group's
+// leaf vector; an uneven member maps each padded row to its own row (or to none:
+// zero going in, dropped coming out)
 __global__ void gather_scatter_kernel(const double* const* ptrs, const long long* rows,
                                       const double* const* group_vec, const long long* group_ld,
-                                      int nc, int col0, int scatter) {
+                                      const int* const* maps, const long long* user_n, int nc,
+                                      int col0, int scatter) {
   const int i = blockIdx.x;
   const long long n = rows[2 * i], off = rows[2 * i + 1];
   double* gv = const_cast<double*>(group_vec[i]);
-  const long long ldg = group_ld[i];
+  const long long ldg = group_ld[i], un = user_n[i];
+  const int* map = maps[i];
   double* user = const_cast<double*>(ptrs[i]);
   for (long long e = threadIdx.x; e < n * nc; e += blockDim.x) {
     const long long k = e % n, j = e / n;
-    double* a = user + k + (long long)(col0 + j) * n;
+    const long long q = map ? map[k] : k;
     double* g = gv + off + k + j * ldg;
-    if (scatter) *a = *g; else *g = *a;
+    if (scatter) {
+      if (q >= 0) user[q + (long long)(col0 + j) * un] = *g;
+    } else {
+      *g = q >= 0 ? user[q + (long long)(col0 + j) * un] : 0.0;
+    }
   }
 }
 
@@ -376,13 +390,30 @@ int hss_batch_create(int32_t count, const hss_shape* shapes, const double* const
                      hss_batch_t* out) {
   if (!out || count <= 0 || !shapes || !D || !U || !S || !E) return HSS_ERR_INVALID_ARG;
   *out = nullptr;
+  // uneven members: generators embedded in the uniform (leaf, rank) layout
+  std::vector<UnevenPad> pads(count);
+  std::vector<const double*> Dp(D, D + count), Up(U, U + count), Ep(E, E + count),
+      Sp(S, S + count);
   for (int i = 0; i < count; ++i) {
     const hss_shape& s = shapes[i];
     if (s.levels < 1 || s.levels > 24 || s.leaf < 1 || s.leaf > 768 || s.rank < 1 ||
-        s.rank > s.leaf || s.rank > 256 || (long long)s.leaf << s.levels != (long long)s.n)
+        s.rank > s.leaf || s.rank > 256)
       return HSS_ERR_INVALID_ARG;
     if (!D[i] || !U[i] || !S[i] || (s.levels >= 2 && !E[i])) return HSS_ERR_INVALID_ARG;
+    if (s.node_sizes) {
+      if (pad_uneven(s, D[i], U[i], E[i], S[i], &pads[i]) != HSS_OK) return HSS_ERR_INVALID_ARG;
+      Dp[i] = pads[i].D.data();
+      Up[i] = pads[i].U.data();
+      Ep[i] = pads[i].E.data();
+      Sp[i] = pads[i].S.data();
+    } else if ((long long)s.leaf << s.levels != (long long)s.n) {
+      return HSS_ERR_INVALID_ARG;
+    }
   }
+  D = Dp.data();
+  U = Up.data();
+  E = Ep.data();
+  S = Sp.data();
   hss_batch_s* bt = new (std::nothrow) hss_batch_s();
   if (!bt) return HSS_ERR_OOM;
   bt->count = count;
@@ -435,7 +466,7 @@ int hss_batch_create(int32_t count, const hss_shape* shapes, const double* const
       const hss_shape& s = shapes[i];
       const long long nl = 1LL << L;
       g.row_off[m] = node_off[0] * leaf;
-      prow[2 * i] = s.n;
+      prow[2 * i] = nl * leaf;   // rows of the (padded) uniform tree
       prow[2 * i + 1] = g.row_off[m];
       gvec[i] = g.xg;
       gld[i] = g.rows;
@@ -503,6 +534,36 @@ int hss_batch_create(int32_t count, const hss_shape* shapes, const double* const
   e = e ? e : cudaMemcpy(bt->ptr_rows + 2 * count, gld.data(), sizeof(long long) * count,
                          cudaMemcpyHostToDevice);
   e = e ? e : cudaMemset(bt->status, 0, 8 * sizeof(int));
+  {   // row maps of uneven members, their table, the callers' orders
+    long long map_ints = 0;
+    for (int i = 0; i < count; ++i) map_ints += (long long)pads[i].pmap.size();
+    const size_t tab = sizeof(int*) * count, un = sizeof(long long) * count;
+    if (e == cudaSuccess && cudaMalloc(&bt->map_mem, tab + un + sizeof(int) * (map_ints + 1)) !=
+                                cudaSuccess) {
+      cudaGetLastError();
+      hss_batch_destroy(bt);
+      return HSS_ERR_OOM;
+    }
+    if (e == cudaSuccess) {
+      char* base = static_cast<char*>(bt->map_mem);
+      bt->map_tab = reinterpret_cast<const int**>(base);
+      bt->user_n = reinterpret_cast<long long*>(base + tab);
+      int* maps = reinterpret_cast<int*>(base + tab + un);
+      std::vector<const int*> mt(count, nullptr);
+      std::vector<long long> nn(count);
+      long long o = 0;
+      for (int i = 0; i < count; ++i) {
+        nn[i] = shapes[i].n;
+        if (pads[i].pmap.empty()) continue;
+        mt[i] = maps + o;
+        e = e ? e : cudaMemcpy(maps + o, pads[i].pmap.data(), sizeof(int) * pads[i].pmap.size(),
+                               cudaMemcpyHostToDevice);
+        o += (long long)pads[i].pmap.size();
+      }
+      e = e ? e : cudaMemcpy(bt->map_tab, mt.data(), tab, cudaMemcpyHostToDevice);
+      e = e ? e : cudaMemcpy(bt->user_n, nn.data(), un, cudaMemcpyHostToDevice);
+    }
+  }
   for (Group& g : bt->groups) {
     g.ev.assign(g.H, nullptr);
     e = e ? e : cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking);
@@ -540,6 +601,7 @@ void hss_batch_destroy(hss_batch_t bt) {
   if (bt->ev_cap_out) cudaEventDestroy(bt->ev_cap_out);
   if (bt->cap_stream) cudaStreamDestroy(bt->cap_stream);
   cudaFree(bt->arena);
+  if (bt->map_mem) cudaFree(bt->map_mem);
   delete bt;
 }
 
@@ -617,7 +679,8 @@ int hss_batch_solve(hss_batch_t bt, const double* const* b, double* const* x, in
       return HSS_ERR_CUDA;
     gather_scatter_kernel<<<count, 256, 0, st>>>(bt->ptr_tab, bt->ptr_rows,
                                                  bt->ptr_tab + count,
-                                                 bt->ptr_rows + 2 * count, nc, j0, 0);
+                                                 bt->ptr_rows + 2 * count, bt->map_tab,
+                                                 bt->user_n, nc, j0, 0);
     int rc = fork_join(bt, st, [&](Group& g) { return solve_group(g, nc); });
     if (rc) return rc;
     if (cudaMemcpyAsync(bt->ptr_tab, xp.data(), sizeof(double*) * count, cudaMemcpyHostToDevice,
@@ -625,7 +688,8 @@ int hss_batch_solve(hss_batch_t bt, const double* const* b, double* const* x, in
       return HSS_ERR_CUDA;
     gather_scatter_kernel<<<count, 256, 0, st>>>(bt->ptr_tab, bt->ptr_rows,
                                                  bt->ptr_tab + count,
-                                                 bt->ptr_rows + 2 * count, nc, j0, 1);
+                                                 bt->ptr_rows + 2 * count, bt->map_tab,
+                                                 bt->user_n, nc, j0, 1);
     if (cudaGetLastError() != cudaSuccess) return HSS_ERR_CUDA;
     // the pointer table is reused by the next pass: keep the host copies alive until then
     if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;

@@ -21,6 +21,7 @@
 #include "ir_kernels.cuh"
 #include "tc_gemm.cuh"
 #include "ulv_kernels.cuh"
+#include "uneven.cuh"
 
 #include <type_traits>
 
@@ -61,7 +62,11 @@ struct Factor {
 }  // namespace
 
 struct hss_s {
-  int n = 0, leaf = 0, rank = 0, L = 0;
+  int n = 0, leaf = 0, rank = 0, L = 0;   // n: order of the (padded) uniform tree
+  int n_user = 0;                      // order of the caller's matrix (= n unless uneven)
+  int uneven = 0;                      // an uneven tree embedded in the uniform one
+  int* pmap = nullptr;                 // n entries: caller's row of each padded row, or -1
+  double *vin = nullptr, *vout = nullptr;   // padded vectors (n x kMaxCols) of uneven calls
   int device = 0;
   double *D = nullptr, *U = nullptr, *E = nullptr, *S = nullptr;
   long long esz = 0, ssz = 0;
@@ -224,6 +229,11 @@ size_t layout_main(hss_s* h, char* base) {
   h->status = bp.take<int>(8);
   h->tree_cnt = bp.take<int>(size_t(2) << kTreeTop);
   h->tree_ready = bp.take<int>(size_t(2) << kTreeTop);
+  if (h->uneven) {
+    h->pmap = bp.take<int>((size_t)h->n);
+    h->vin = bp.take<double>((size_t)h->n * kMaxCols);
+    h->vout = bp.take<double>((size_t)h->n * kMaxCols);
+  }
   return bp.off + 256;
 }
 
@@ -970,11 +980,25 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   const int L = shape->levels, leaf = shape->leaf, r = shape->rank;
   if (L < 1 || L > 24 || leaf < 1 || leaf > 768 || r < 1 || r > leaf || r > 256)
     return HSS_ERR_INVALID_ARG;
-  if ((long long)leaf << L != (long long)shape->n) return HSS_ERR_INVALID_ARG;
   if (L >= 2 && !E) return HSS_ERR_INVALID_ARG;
+  // an uneven tree: its generators embedded in the uniform (leaf, rank) ones
+  UnevenPad pad;
+  if (shape->node_sizes) {
+    if (on_device || (long long)leaf << L > 0x7fffffffLL) return HSS_ERR_INVALID_ARG;
+    const int rc = pad_uneven(*shape, D, U, E, S, &pad);
+    if (rc) return rc;
+    D = pad.D.data();
+    U = pad.U.data();
+    E = pad.E.data();
+    S = pad.S.data();
+  } else if ((long long)leaf << L != (long long)shape->n) {
+    return HSS_ERR_INVALID_ARG;
+  }
   hss_s* h = new (std::nothrow) hss_s();
   if (!h) return HSS_ERR_OOM;
-  h->n = shape->n;
+  h->n = (int)((long long)leaf << L);
+  h->n_user = shape->n;
+  h->uneven = shape->node_sizes ? 1 : 0;
   h->leaf = leaf;
   h->rank = r;
   h->L = L;
@@ -998,6 +1022,8 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   e = e ? e : cudaMemcpy(h->S, S, sizeof(double) * h->ssz, kind);
   e = e ? e : cudaMemset(h->status, 0, 8 * sizeof(int));
   e = e ? e : cudaMemset(h->tree_ready, 0, sizeof(int) << (kTreeTop + 1));
+  if (h->uneven)
+    e = e ? e : cudaMemcpy(h->pmap, pad.pmap.data(), sizeof(int) * h->n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(mem);
     delete h;
@@ -1100,12 +1126,12 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
   return HSS_OK;
 }
 
-int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, void* stream) {
-  if (!h || !b || !x || nrhs < 0 || ld < h->n) return HSS_ERR_INVALID_ARG;
-  if (!h->factorized) return HSS_ERR_NOT_FACTORIZED;
-  if (nrhs == 0) return HSS_OK;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  h->last_stream = st;
+}  // extern "C"
+
+namespace {
+
+// the solve of a uniform tree (or of the padded one, on padded vectors)
+int solve_uniform(hss_t h, const double* b, double* x, int nrhs, int ld, cudaStream_t st) {
   if (h->precision != HSS_FP64) return solve_ir(h, b, x, nrhs, ld, st);
   if (x != b) {
     cudaError_t e = cudaMemcpy2DAsync(x, sizeof(double) * ld, b, sizeof(double) * ld,
@@ -1120,23 +1146,70 @@ int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, voi
   return HSS_OK;
 }
 
-int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, void* stream) {
-  if (!h || !x || !y || nrhs < 0 || ld < h->n || x == y) return HSS_ERR_INVALID_ARG;
+// Runs op(in, out, nc) on the padded vectors of an uneven tree, cols columns
+// per pass: the caller's rows of x scattered in (zero padded rows), out
+// gathered back into y.  A no-convergence result is carried to the end.
+template <typename Op>
+int on_padded(hss_t h, const double* x, double* y, int nrhs, int ld, int cols, cudaStream_t st,
+              Op op) {
+  int result = HSS_OK, worst_it = 0;
+  double worst_res = 0.0;
+  for (int j0 = 0; j0 < nrhs; j0 += cols) {
+    const int nc = std::min(cols, nrhs - j0);
+    launch_pad_rows(x + (long long)j0 * ld, ld, h->vin, h->n, h->pmap, h->n, nc, 1, st);
+    const int rc = op(h->vin, h->vout, nc);
+    if (rc && rc != HSS_ERR_NO_CONVERGENCE) return rc;
+    if (rc) result = rc;
+    worst_it = std::max(worst_it, h->ir_iters);
+    worst_res = std::max(worst_res, h->ir_resid);
+    launch_pad_rows(y + (long long)j0 * ld, ld, h->vout, h->n, h->pmap, h->n, nc, 0, st);
+    if (cudaGetLastError() != cudaSuccess) return HSS_ERR_CUDA;
+  }
+  h->ir_iters = worst_it;
+  h->ir_resid = worst_res;
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, void* stream) {
+  if (!h || !b || !x || nrhs < 0 || ld < h->n_user) return HSS_ERR_INVALID_ARG;
+  if (!h->factorized) return HSS_ERR_NOT_FACTORIZED;
   if (nrhs == 0) return HSS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->last_stream = st;
-  return matvec_fp64(h, x, ld, y, ld, nrhs, st);
+  if (!h->uneven) return solve_uniform(h, b, x, nrhs, ld, st);
+  return on_padded(h, b, x, nrhs, ld, kSolveCols, st, [&](const double* in, double* out, int nc) {
+    return solve_uniform(h, in, out, nc, h->n, st);
+  });
+}
+
+int hss_matvec(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld, void* stream) {
+  if (!h || !x || !y || nrhs < 0 || ld < h->n_user || x == y) return HSS_ERR_INVALID_ARG;
+  if (nrhs == 0) return HSS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->last_stream = st;
+  if (!h->uneven) return matvec_fp64(h, x, ld, y, ld, nrhs, st);
+  return on_padded(h, x, y, nrhs, ld, kMaxCols, st, [&](const double* in, double* out, int nc) {
+    return matvec_fp64(h, in, h->n, out, h->n, nc, st);
+  });
 }
 
 int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t ld,
                     void* stream) {
-  if (!h || !x || !y || nrhs < 0 || ld < h->n || x == y) return HSS_ERR_INVALID_ARG;
+  if (!h || !x || !y || nrhs < 0 || ld < h->n_user || x == y) return HSS_ERR_INVALID_ARG;
   if (nrhs == 0) return HSS_OK;
   int rc = ensure_f32_arena(h);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->last_stream = st;
   if (!h->pairs_valid && split_generators(h, st, SPLIT_ALL) != cudaSuccess) return HSS_ERR_CUDA;
+  if (h->uneven)
+    return on_padded(h, x, y, nrhs, ld, kSolveCols, st, [&](const double* in, double* out, int nc) {
+      return matvec_pair(h, in, h->n, out, h->n, nc, st);
+    });
   for (int j0 = 0; j0 < nrhs; j0 += kSolveCols) {
     const int nc = std::min(kSolveCols, nrhs - j0);
     rc = matvec_pair(h, x + (long long)j0 * ld, ld, y + (long long)j0 * ld, ld, nc, st);

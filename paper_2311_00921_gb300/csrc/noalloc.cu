@@ -50,6 +50,7 @@ extern "C" int hss_matvec_noalloc(const hss_shape* shape, const double* D, const
                                   const double* E, const double* S, const double* x, double* y,
                                   int32_t nrhs, int32_t ld, void* stream) {
   if (!shape || !D || !U || !S || !x || !y || x == y || nrhs < 0) return HSS_ERR_INVALID_ARG;
+  if (shape->node_sizes) return HSS_ERR_INVALID_ARG;   // uniform trees only
   const int L = shape->levels, leaf = shape->leaf, r = shape->rank;
   if (L < 1 || L > 24 || leaf < 1 || r < 1 || r > leaf) return HSS_ERR_INVALID_ARG;
   if ((long long)leaf << L != (long long)shape->n || ld < shape->n) return HSS_ERR_INVALID_ARG;

@@ -27,7 +27,7 @@ _c_int, _c_double, _p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
 class Shape(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("leaf", ctypes.c_int32), ("rank", ctypes.c_int32),
-                ("levels", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("node_sizes", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Options(ctypes.Structure):
@@ -137,21 +137,52 @@ def colmajor(x, device="cuda"):
     return t.t().contiguous().to(device).t()
 
 
+def uneven_shape(h):
+    """(shape, D, U, E, S, sizes) of a non-uniform tree for hss_create: node_sizes =
+    the leaf orders, leaf = the largest of them (at least the rank), rank = the
+    largest rank, generators
+    packed block after block (each column-major).  The ranks must follow
+    r_i = min(rank, b_i) at the leaves and min(rank, r_c1 + r_c2) above."""
+    L = h.levels
+    sizes = np.asarray(h.sizes, dtype=np.int32)
+    rank = int(max(int(np.max(v)) for v in h.ranks.values()))
+    rk = {L: np.minimum(rank, sizes)}
+    for l in range(L - 1, 0, -1):
+        rk[l] = np.minimum(rank, rk[l + 1][0::2] + rk[l + 1][1::2])
+    for l in range(1, L + 1):
+        if not np.array_equal(np.asarray(h.ranks[l]), rk[l]):
+            raise ValueError("ranks do not follow min(rank, order) of an uneven tree")
+    flat = lambda blocks: np.concatenate([np.asarray(b, dtype=np.float64).T.ravel()
+                                          for b in blocks])
+    D, U = flat(h.D), flat(h.U)
+    E = (np.concatenate([flat(h.E[l]) for l in range(1, L)]) if L >= 2 else np.zeros(1))
+    S = np.concatenate([flat(h.S[l]) for l in range(1, L + 1)])
+    keep = np.ascontiguousarray(sizes)
+    # the padded leaf order holds the largest leaf and the rank's basis columns
+    shape = Shape(h.n, int(max(sizes.max(), rank)), rank, L,
+                  keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return shape, D, U, E, S, keep
+
+
 class HSS:
-    """A device-resident HSS matrix (generators copied at construction)."""
+    """A device-resident HSS matrix (generators copied at construction); uniform
+    or uneven trees (the library embeds an uneven one in the uniform format)."""
 
     def __init__(self, h):
-        if not h.uniform:
-            raise ValueError("the CUDA library takes uniform trees")
         lib = load()
-        L, r, leaf = h.levels, h.rank, h.leaf
+        L = h.levels
+        if h.uniform:
+            r, leaf = h.rank, h.leaf
+            D = _colmajor_blocks(h.D)
+            U = _colmajor_blocks(h.U)
+            E = (np.concatenate([_colmajor_blocks(h.E[l]).ravel() for l in range(1, L)])
+                 if L >= 2 else np.zeros(1))
+            S = np.concatenate([_colmajor_blocks(h.S[l]).ravel() for l in range(1, L + 1)])
+            shape = Shape(h.n, leaf, r, L)
+        else:
+            shape, D, U, E, S, _keep = uneven_shape(h)
+            r, leaf = shape.rank, shape.leaf
         self.n, self.levels, self.rank, self.leaf = h.n, L, r, leaf
-        D = _colmajor_blocks(h.D)
-        U = _colmajor_blocks(h.U)
-        E = (np.concatenate([_colmajor_blocks(h.E[l]).ravel() for l in range(1, L)])
-             if L >= 2 else np.zeros(1))
-        S = np.concatenate([_colmajor_blocks(h.S[l]).ravel() for l in range(1, L + 1)])
-        shape = Shape(h.n, leaf, r, L)
         out = _p()
         _check(lib.hss_create(ctypes.byref(shape), D.ctypes.data, U.ctypes.data, E.ctypes.data,
                               S.ctypes.data, 0, ctypes.byref(out)), "hss_create")
@@ -306,14 +337,22 @@ def matvec_noalloc(shape, D, U, E, S, x, y, stream=None):
 
 class HSSBatch:
     """Many device-resident HSS matrices of uneven shapes, factored and solved
-    together (hss_batch_*)."""
+    together (hss_batch_*); members may be uniform or uneven trees."""
 
     def __init__(self, mats):
         lib = load()
         self.count = len(mats)
         self.n = [h.n for h in mats]
-        shapes = (Shape * self.count)(*[Shape(h.n, h.leaf, h.rank, h.levels) for h in mats])
-        self._keep = [packed_generators(h) for h in mats]
+        shp, self._keep = [], []
+        for h in mats:
+            if h.uniform:
+                shp.append(Shape(h.n, h.leaf, h.rank, h.levels))
+                self._keep.append(packed_generators(h))
+            else:
+                s, D, U, E, S, sizes = uneven_shape(h)
+                shp.append(s)
+                self._keep.append((D, U, E, S, sizes))
+        shapes = (Shape * self.count)(*shp)
         arr = lambda k: (_p * self.count)(*[a[k].ctypes.data for a in self._keep])
         out = _p()
         _check(lib.hss_batch_create(self.count, shapes, arr(0), arr(1), arr(2), arr(3),

@@ -94,13 +94,15 @@ def make_points(w: Workload, rng: np.random.Generator) -> np.ndarray:
         g = rng.standard_normal((n, 3))
         return g / np.linalg.norm(g, axis=1, keepdims=True)
     if w.geometry == "grid2d":
-        # sx x sy jittered grid of the unit square (sx = sy when n is a square)
+        # sx x sy jittered grid of the unit square (sx = sy when n is a square;
+        # else a power-of-two sx when it divides n, else the largest divisor of
+        # n not above sqrt(n))
         sx = int(round(math.sqrt(n)))
         if sx * sx != n:
             sx = 1 << int(math.ceil(math.log2(n) / 2))
+        if n % sx:
+            sx = max(d for d in range(1, int(math.isqrt(n)) + 1) if n % d == 0)
         sy = n // sx
-        if sx * sy != n:
-            raise ValueError("grid2d needs n = sx * sy")
         i, j = np.meshgrid(np.arange(sx), np.arange(sy), indexing="ij")
         jit = rng.uniform(-0.25, 0.25, size=(2, sx, sy))
         p = np.stack([(i + 0.5 + jit[0]) / sx, (j + 0.5 + jit[1]) / sy], -1)
@@ -166,8 +168,9 @@ class HSSMatrix:
 
     @property
     def uniform(self) -> bool:
+        """One leaf order and one rank at every node of every level."""
         return (len(set(self.sizes.tolist())) == 1 and
-                all(len(set(v.tolist())) == 1 for v in self.ranks.values()))
+                len({int(x) for v in self.ranks.values() for x in v}) == 1)
 
     @property
     def leaf(self) -> int:
