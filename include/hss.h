@@ -117,7 +117,8 @@ typedef enum { HSS_RESIDUAL_FP64 = 0, HSS_RESIDUAL_PAIR32 = 1 } hss_residual;
  * Gram matrix is not numerically positive definite in the working precision,
  * and ranks too large for the per-node kernels (above 165 in FP64, 234 in
  * FP32), use the Householder kernel. */
-typedef enum { HSS_BASIS_HOUSEHOLDER = 0, HSS_BASIS_CHOLQR = 1 } hss_basis_method;
+typedef enum { HSS_BASIS_HOUSEHOLDER = 0, HSS_BASIS_CHOLQR = 1,
+               HSS_BASIS_AUTO = 2 /* the choice of hss_tune, else HOUSEHOLDER */ } hss_basis_method;
 
 /* Schedule of the solve's upper levels (the levels of at most 64 nodes above
  * the leaves).  HSS_SCHEDULE_ASYNC: one launch per direction for all of them,
@@ -127,7 +128,9 @@ typedef enum { HSS_BASIS_HOUSEHOLDER = 0, HSS_BASIS_CHOLQR = 1 } hss_basis_metho
  * parent's ready flag (a bounded wait, see wait_budget; an expired wait makes
  * the solve report HSS_ERR_TIMEOUT).  HSS_SCHEDULE_LEVELS: one launch per level
  * and direction.  Both give the same result. */
-typedef enum { HSS_SCHEDULE_ASYNC = 0, HSS_SCHEDULE_LEVELS = 1 } hss_schedule;
+typedef enum { HSS_SCHEDULE_ASYNC = 0, HSS_SCHEDULE_LEVELS = 1,
+               HSS_SCHEDULE_AUTO = 2 /* the choices of hss_tune (schedule and the sweeps'
+                                        panel staging), else ASYNC */ } hss_schedule;
 
 typedef struct {
   int32_t precision;   /* hss_precision */
@@ -235,6 +238,36 @@ int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t l
 int hss_matvec_noalloc(const hss_shape* shape, const double* D, const double* U, const double* E,
                        const double* S, const double* x, double* y, int32_t nrhs, int32_t ld,
                        void* stream);
+
+/* Choices of the autotuner (hss_tune) for one object: the basis method, the
+ * schedule of the solve's upper levels, the panel staging of the solve's sweep
+ * kernels (0 = the largest shared-memory panels, 1 = the panels that let the
+ * fewest waves of CTAs cover a level), and the measured times of the chosen
+ * configuration. */
+typedef struct {
+  int32_t basis;      /* hss_basis_method */
+  int32_t schedule;   /* hss_schedule */
+  int32_t staging;    /* 0 or 1 */
+  int32_t from_cache; /* 1 when read from the cache file instead of measured */
+  double factor_ms;   /* one factorization with the chosen basis method */
+  double solve_ms;    /* one solve of min(nrhs, 16) columns with the chosen schedule */
+} hss_tuning;
+
+/* Autotuner: for the object's shape and the arithmetic of opt (precision,
+ * residual), times every candidate configuration on the object itself with
+ * CUDA events on `stream` -- each basis method on hss_factorize, each pair of
+ * solve schedule and sweep panel staging on hss_solve of min(nrhs, 16)
+ * columns of a fixed test vector -- best of two runs each, and keeps the
+ * fastest; later hss_factorize calls with basis = HSS_BASIS_AUTO or schedule =
+ * HSS_SCHEDULE_AUTO use them.  cache_path (may be NULL): a text file of
+ * earlier choices, one line per key (device name, precision, residual, n,
+ * leaf, rank, levels, columns); a matching line is used instead of measuring,
+ * and a new measurement is appended.  Leaves the object factorized with the
+ * chosen configuration.  Allocates two n x 16 vectors for the duration of the
+ * call.  Synchronous.  out may be NULL.  Errors: as hss_factorize and
+ * hss_solve, OOM. */
+int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_path, void* stream,
+             hss_tuning* out);
 
 /* Block until the object's work is done and report any device-side failure
  * (HSS_ERR_NOT_SPD ...). */

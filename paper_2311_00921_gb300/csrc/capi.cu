@@ -8,6 +8,7 @@
 // templated on the arithmetic type: double for HSS_FP64, float for the mixed
 // modes (whose root Cholesky, residual and update stay in double).
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -100,6 +101,9 @@ struct hss_s {
   int residual = HSS_RESIDUAL_FP64;    // arithmetic of the refinement residual
   int basis_method = HSS_BASIS_HOUSEHOLDER;   // method of the basis completion
   int schedule = HSS_SCHEDULE_ASYNC;   // launches of the solve's upper levels
+  int staging = 0;                     // panel staging of the sweep kernels (see launch_ulv_fwd)
+  int tuned = 0;                       // hss_tune has chosen the following
+  int tuned_basis = HSS_BASIS_HOUSEHOLDER, tuned_schedule = HSS_SCHEDULE_ASYNC, tuned_staging = 0;
   int* tree_cnt = nullptr;             // arrival counts of the tree forward sweep
   int* tree_ready = nullptr;           // ready flags of the tree backward sweep
   int tree_epoch = 0;
@@ -649,7 +653,7 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
              sizeof(T) == 4);
     HSS_TRY(launch_ulv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
                               Q.n * Q.b, r, fused ? P.V : nullptr, (long long)P.b * r, P.T_,
-                              (long long)r * r, r, P.n, st));
+                              (long long)r * r, r, P.n, st, h->staging));
   }
   if (lo >= 1) {
     Launch k(h, HSS_K_TRSV_FWD, tree_flops, st, sizeof(T) == 4);
@@ -705,7 +709,7 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
                sizeof(T) == 4);
       HSS_TRY(launch_ulv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
                                 Q.n * Q.b, r, fused ? P.V : nullptr, (long long)P.b * r, P.T_,
-                                (long long)r * r, r, P.n, st));
+                                (long long)r * r, r, P.n, st, h->staging));
     }
     if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/false, st);
   }
@@ -1076,9 +1080,9 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
   if (opt && (opt->ir_max_it < 0 || !(opt->ir_tol >= 0.0))) return HSS_ERR_INVALID_ARG;
   if (opt && opt->residual != HSS_RESIDUAL_FP64 && opt->residual != HSS_RESIDUAL_PAIR32)
     return HSS_ERR_INVALID_ARG;
-  if (opt && opt->basis != HSS_BASIS_HOUSEHOLDER && opt->basis != HSS_BASIS_CHOLQR)
+  if (opt && (opt->basis < HSS_BASIS_HOUSEHOLDER || opt->basis > HSS_BASIS_AUTO))
     return HSS_ERR_INVALID_ARG;
-  if (opt && opt->schedule != HSS_SCHEDULE_ASYNC && opt->schedule != HSS_SCHEDULE_LEVELS)
+  if (opt && (opt->schedule < HSS_SCHEDULE_ASYNC || opt->schedule > HSS_SCHEDULE_AUTO))
     return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
@@ -1091,12 +1095,17 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     h->ir_tol = opt->ir_tol;
     h->residual = opt->residual;
     h->wait_budget = opt->wait_budget;
-    h->basis_method = opt->basis;
-    h->schedule = opt->schedule;
+    h->basis_method = opt->basis == HSS_BASIS_AUTO
+                          ? (h->tuned ? h->tuned_basis : HSS_BASIS_HOUSEHOLDER)
+                          : opt->basis;
+    const bool sauto = opt->schedule == HSS_SCHEDULE_AUTO;
+    h->schedule = sauto ? (h->tuned ? h->tuned_schedule : HSS_SCHEDULE_ASYNC) : opt->schedule;
+    h->staging = sauto && h->tuned ? h->tuned_staging : 0;
   } else {
     h->wait_budget = 0;
     h->basis_method = HSS_BASIS_HOUSEHOLDER;
     h->schedule = HSS_SCHEDULE_ASYNC;
+    h->staging = 0;
   }
   h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
   h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;
@@ -1215,6 +1224,133 @@ int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t l
     rc = matvec_pair(h, x + (long long)j0 * ld, ld, y + (long long)j0 * ld, ld, nc, st);
     if (rc) return rc;
   }
+  return HSS_OK;
+}
+
+int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_path, void* stream,
+             hss_tuning* out) {
+  if (!h || !opt || nrhs < 1) return HSS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nc = std::min<int>(nrhs, kSolveCols);
+  hss_tuning best{};
+  // cache key
+  char key[512];
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return HSS_ERR_CUDA;
+    char dev[256];
+    int q = 0;
+    for (const char* c = prop.name; *c && q < 255; ++c) dev[q++] = (*c == ' ' ? '_' : *c);
+    dev[q] = 0;
+    snprintf(key, sizeof key, "%s p%d res%d n%d leaf%d rank%d L%d cols%d", dev, opt->precision,
+             opt->residual, h->n_user, h->leaf, h->rank, h->L, nc);
+  }
+  bool found = false;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[1024];
+      const size_t kl = strlen(key);
+      while (fgets(line, sizeof line, f)) {
+        if (strncmp(line, key, kl) != 0 || line[kl] != ' ') continue;
+        hss_tuning t{};
+        if (sscanf(line + kl, " basis %d schedule %d staging %d factor_ms %lf solve_ms %lf",
+                   &t.basis, &t.schedule, &t.staging, &t.factor_ms, &t.solve_ms) == 5 &&
+            t.basis >= HSS_BASIS_HOUSEHOLDER && t.basis <= HSS_BASIS_CHOLQR &&
+            t.schedule >= HSS_SCHEDULE_ASYNC && t.schedule <= HSS_SCHEDULE_LEVELS &&
+            (t.staging == 0 || t.staging == 1)) {
+          best = t;
+          best.from_cache = 1;
+          found = true;
+        }
+      }
+      fclose(f);
+    }
+  }
+  hss_options o = *opt;
+  if (!found) {
+    double* buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * 2 * (size_t)h->n_user * kSolveCols) != cudaSuccess) {
+      cudaGetLastError();
+      return HSS_ERR_OOM;
+    }
+    double* b = buf;
+    double* x = buf + (size_t)h->n_user * kSolveCols;
+    launch_fill_test(b, h->n_user, nc, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
+                 ? HSS_OK
+                 : HSS_ERR_CUDA;
+    // best of two timed runs of fn (after one untimed run)
+    auto timed = [&](auto&& fn, double* ms) -> int {
+      int r = fn();
+      if (r && r != HSS_ERR_NO_CONVERGENCE) return r;
+      *ms = 1e30;
+      for (int t = 0; t < 2; ++t) {
+        if (cudaEventRecord(e0, st) != cudaSuccess) return HSS_ERR_CUDA;
+        r = fn();
+        if (r && r != HSS_ERR_NO_CONVERGENCE) return r;
+        float v = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&v, e0, e1) != cudaSuccess)
+          return HSS_ERR_CUDA;
+        *ms = std::min(*ms, (double)v);
+      }
+      return hss_sync(h);
+    };
+    best.factor_ms = 1e30;
+    const bool cholqr_ok = o.precision == HSS_FP64 ? h->rank <= basis_max_rank<double>()
+                                                  : h->rank <= basis_max_rank<float>();
+    for (int basis = HSS_BASIS_HOUSEHOLDER; rc == HSS_OK && basis <= HSS_BASIS_CHOLQR; ++basis) {
+      if (basis == HSS_BASIS_CHOLQR && !cholqr_ok) continue;
+      o.basis = basis;
+      o.schedule = HSS_SCHEDULE_ASYNC;
+      double ms = 0.0;
+      rc = timed([&] { return hss_factorize(h, &o, st); }, &ms);
+      if (rc == HSS_OK && ms < best.factor_ms) {
+        best.factor_ms = ms;
+        best.basis = basis;
+      }
+    }
+    if (rc == HSS_OK) {
+      o.basis = best.basis;
+      rc = hss_factorize(h, &o, st);
+    }
+    best.solve_ms = 1e30;
+    for (int sched = HSS_SCHEDULE_ASYNC; rc == HSS_OK && sched <= HSS_SCHEDULE_LEVELS; ++sched) {
+      for (int stg = 0; rc == HSS_OK && stg <= 1; ++stg) {
+        h->schedule = sched;
+        h->staging = stg;
+        double ms = 0.0;
+        rc = timed([&] { return hss_solve(h, b, x, nc, h->n_user, st); }, &ms);
+        if (rc == HSS_OK && ms < best.solve_ms) {
+          best.solve_ms = ms;
+          best.schedule = sched;
+          best.staging = stg;
+        }
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (rc) return rc;
+    if (cache_path) {
+      if (FILE* f = fopen(cache_path, "a")) {
+        fprintf(f, "%s basis %d schedule %d staging %d factor_ms %.4f solve_ms %.4f\n", key,
+                best.basis, best.schedule, best.staging, best.factor_ms, best.solve_ms);
+        fclose(f);
+      }
+    }
+  }
+  h->tuned = 1;
+  h->tuned_basis = best.basis;
+  h->tuned_schedule = best.schedule;
+  h->tuned_staging = best.staging;
+  o.basis = HSS_BASIS_AUTO;
+  o.schedule = HSS_SCHEDULE_AUTO;
+  const int rc = hss_factorize(h, &o, st);
+  if (rc) return rc;
+  if (out) *out = best;
   return HSS_OK;
 }
 

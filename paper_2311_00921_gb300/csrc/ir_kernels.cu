@@ -130,3 +130,14 @@ void launch_col_norms(const double* v, int ld, int m, int nc, double* norms, dou
 void launch_eye(double* a, int n, cudaStream_t st) {
   eye_kernel<<<grid_for((long long)n * n), NT, 0, st>>>(a, n);
 }
+
+__global__ void fill_test_kernel(double* x, int n, int nc) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT)
+    x[i + (long long)j * n] = sin(0.37 * i + 1.7 * j) + 0.25 * cos(0.011 * i * (j + 1));
+}
+
+void launch_fill_test(double* x, int n, int nc, cudaStream_t st) {
+  if (n <= 0 || nc <= 0) return;
+  fill_test_kernel<<<dim3(grid_for(n), nc), NT, 0, st>>>(x, n, nc);
+}

@@ -16,3 +16,5 @@ void launch_residual(const double* b, int ldb, double* r, int ldr, int m, int nc
 void launch_col_norms(const double* v, int ld, int m, int nc, double* norms, double* inv,
                       double* scratch, cudaStream_t st);
 void launch_eye(double* a, int n, cudaStream_t st);   // a = I (n x n, column-major)
+// a fixed, deterministic n x nc test block (column-major, ld n)
+void launch_fill_test(double* x, int n, int nc, cudaStream_t st);

@@ -1281,31 +1281,54 @@ size_t trsv_smem(int b, int nrhs, int r, int CB, int NBUF, bool bwd) {
   return (vec + rowmajor + (size_t)32 * r + (size_t)NBUF * (b | 1) * CB) * sizeof(T);
 }
 
-// the largest staging the device allows: two 32-column panels, else one, else
-// 16- and 8-column panels
+// Panel staging of a sweep launch of `nodes` CTAs.  staging = 0: the largest
+// the device allows (two 32-column panels, else one, else 16- and 8-column
+// panels).  staging = 1: the fewest waves of CTAs over the SMs (smaller panels
+// let more CTAs share an SM), ties to the larger staging.
 template <typename T, typename K>
 cudaError_t trsv_config(K kernel, int b, int nrhs, int r, bool bwd, int* CB, int* NBUF,
-                        size_t* sm) {
+                        size_t* sm, int nodes = 1, int staging = 0) {
   const int cbs[5] = {32, 32, 16, 16, 8}, bufs[5] = {2, 1, 2, 1, 1};
-  for (int q = 0; q < 5; ++q) {
-    *CB = cbs[q];
-    *NBUF = bufs[q];
-    *sm = trsv_smem<T>(b, nrhs, r, *CB, *NBUF, bwd);
-    if (smem_opt_in(kernel, *sm)) return cudaSuccess;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || !sms)
+      sms = 1;
   }
-  return cudaErrorInvalidConfiguration;
+  long long best_waves = -1;
+  for (int q = 0; q < 5; ++q) {
+    const size_t s = trsv_smem<T>(b, nrhs, r, cbs[q], bufs[q], bwd);
+    if (!smem_opt_in(kernel, s)) continue;
+    long long waves = 0;
+    if (staging == 1) {
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, NT, s) != cudaSuccess ||
+          occ < 1)
+        occ = 1;
+      waves = (nodes + (long long)sms * occ - 1) / ((long long)sms * occ);
+    }
+    if (best_waves < 0 || waves < best_waves) {
+      best_waves = waves;
+      *CB = cbs[q];
+      *NBUF = bufs[q];
+      *sm = s;
+    }
+    if (staging == 0) break;
+  }
+  return best_waves < 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
 
 template <typename T>
 cudaError_t launch_ulv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                            long long sX, int nrhs, T* Par, int ldpar, long long sPar, const T* V,
                            long long sV, const T* Tm, long long sT, int r, int nodes,
-                           cudaStream_t st) {
+                           cudaStream_t st, int staging) {
   if (nrhs > 16 || (V && (r < 1 || r > NT || r > b))) return cudaErrorInvalidValue;
   int CB, NBUF;
   size_t sm;
   cudaError_t e = trsv_config<T>(trsv_fwd_kernel<T>, b, nrhs, V ? r : 0, false, &CB, &NBUF,
-                                 &sm);
+                                 &sm, nodes, staging);
   if (e != cudaSuccess) return e;
   trsv_fwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, V,
                                             sV, Tm, sT, V ? r : 0, CB, NBUF);
@@ -1316,12 +1339,12 @@ template <typename T>
 cudaError_t launch_ulv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                            long long sX, int nrhs, const T* Par, int ldpar, long long sPar,
                            const T* V, long long sV, const T* Tm, long long sT, int r, int nodes,
-                           cudaStream_t st) {
+                           cudaStream_t st, int staging) {
   if (nrhs > 16 || (V && (r < 1 || r > NT || r > b))) return cudaErrorInvalidValue;
   int CB, NBUF;
   size_t sm;
   cudaError_t e = trsv_config<T>(trsv_bwd_kernel<T>, b, nrhs, V ? r : 0, true, &CB, &NBUF,
-                                 &sm);
+                                 &sm, nodes, staging);
   if (e != cudaSuccess) return e;
   trsv_bwd_kernel<T><<<nodes, NT, sm, st>>>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, V,
                                             sV, Tm, sT, V ? r : 0, CB, NBUF);
@@ -1364,7 +1387,7 @@ cudaError_t launch_trsv_fwd(const T* M, int ldm, long long sM, int b, int c, T* 
                             long long sX, int nrhs, T* Par, int ldpar, long long sPar, int nodes,
                             cudaStream_t st) {
   return launch_ulv_fwd<T>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, nullptr, 0,
-                           nullptr, 0, 0, nodes, st);
+                           nullptr, 0, 0, nodes, st, 0);
 }
 
 template <typename T>
@@ -1372,7 +1395,7 @@ cudaError_t launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* 
                             long long sX, int nrhs, const T* Par, int ldpar, long long sPar,
                             int nodes, cudaStream_t st) {
   return launch_ulv_bwd<T>(M, ldm, sM, b, c, X, ldx, sX, nrhs, Par, ldpar, sPar, nullptr, 0,
-                           nullptr, 0, 0, nodes, st);
+                           nullptr, 0, 0, nodes, st, 0);
 }
 
 void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t st) {
@@ -1391,10 +1414,10 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
                                           int, const T*, int, long long, int, cudaStream_t);      \
   template cudaError_t launch_ulv_fwd<T>(const T*, int, long long, int, int, T*, int, long long,  \
                                          int, T*, int, long long, const T*, long long, const T*,  \
-                                         long long, int, int, cudaStream_t);                      \
+                                         long long, int, int, cudaStream_t, int);                 \
   template cudaError_t launch_ulv_bwd<T>(const T*, int, long long, int, int, T*, int, long long,  \
                                          int, const T*, int, long long, const T*, long long,      \
-                                         const T*, long long, int, int, cudaStream_t);            \
+                                         const T*, long long, int, int, cudaStream_t, int);       \
   template size_t ql_smem<T>(int, int);                                                          \
   template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int, int,\
                                             int*, int, bool, cudaStream_t);                       \

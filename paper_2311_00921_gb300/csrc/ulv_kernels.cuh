@@ -31,17 +31,19 @@ cudaError_t launch_trsv_bwd(const T* M, int ldm, long long sM, int b, int c, T* 
 // sweep (launch_trsv_fwd); the backward sweep runs the triangular backward sweep
 // and then applies Q = I - V T Vᵀ.  V (b x r, batch stride sV) and T (r x r,
 // batch stride sT) are the node's compact-WY basis (Eq. 2-3); V = null skips
-// the Q application.  nrhs <= 16, r <= min(b, 256).
+// the Q application.  nrhs <= 16, r <= min(b, 256).  staging: 0 = the
+// largest panel staging shared memory allows, 1 = the staging that needs the
+// fewest waves of CTAs over the SMs.
 template <typename T>
 cudaError_t launch_ulv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                            long long sX, int nrhs, T* Par, int ldpar, long long sPar, const T* V,
                            long long sV, const T* Tm, long long sT, int r, int nodes,
-                           cudaStream_t st);
+                           cudaStream_t st, int staging = 0);
 template <typename T>
 cudaError_t launch_ulv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                            long long sX, int nrhs, const T* Par, int ldpar, long long sPar,
                            const T* V, long long sV, const T* Tm, long long sT, int r, int nodes,
-                           cudaStream_t st);
+                           cudaStream_t st, int staging = 0);
 
 void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t st);
 

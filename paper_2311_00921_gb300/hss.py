@@ -38,8 +38,14 @@ class Options(ctypes.Structure):
 
 
 RESIDUALS = {"fp64": 0, "pair32": 1}
-BASIS_METHODS = {"householder": 0, "cholqr": 1}
-SCHEDULES = {"async": 0, "levels": 1}
+BASIS_METHODS = {"householder": 0, "cholqr": 1, "auto": 2}
+SCHEDULES = {"async": 0, "levels": 1, "auto": 2}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("basis", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("staging", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("factor_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -51,6 +57,8 @@ SIGNATURES = {
     "hss_matvec": (_c_int, [_p, _p, _p, ctypes.c_int32, ctypes.c_int32, _p]),
     "hss_matvec_pair": (_c_int, [_p, _p, _p, ctypes.c_int32, ctypes.c_int32, _p]),
     "hss_sync": (_c_int, [_p]),
+    "hss_tune": (_c_int, [_p, ctypes.POINTER(Options), ctypes.c_int32, ctypes.c_char_p, _p,
+                          ctypes.POINTER(Tuning)]),
     "hss_last_info": (_c_int, [_p, _i32p, _i32p, _i32p, _i32p, ctypes.POINTER(_c_double)]),
     "hss_export": (_c_int, [_p, ctypes.c_int32, ctypes.c_int32, _p, ctypes.c_size_t]),
     "hss_trace": (_c_int, [_p, ctypes.c_int32]),
@@ -260,6 +268,23 @@ class HSS:
 
     def sync(self):
         _check(load().hss_sync(self._h), "hss_sync")
+
+    def tune(self, precision="fp64", nrhs=16, residual="fp64", cache=None, stream=None):
+        """hss_tune: measure the candidate basis methods, solve schedules and sweep
+        stagings on this object and keep the fastest (used by factorize(...,
+        basis="auto", schedule="auto")).  Returns the choices as a dict."""
+        opt = Options(PRECISIONS[precision], 30, 1e-12, RESIDUALS[residual], 0, 0, 0, 0)
+        t = Tuning()
+        _check(load().hss_tune(self._h, ctypes.byref(opt), nrhs,
+                               cache.encode() if cache else None, _stream_ptr(stream),
+                               ctypes.byref(t)), "hss_tune")
+        self.precision = precision
+        names_b = {v: k for k, v in BASIS_METHODS.items()}
+        names_s = {v: k for k, v in SCHEDULES.items()}
+        return {"basis": names_b[t.basis], "schedule": names_s[t.schedule],
+                "staging": "fewest_waves" if t.staging else "largest_panels",
+                "from_cache": bool(t.from_cache), "factor_ms": t.factor_ms,
+                "solve_ms": t.solve_ms}
 
     def last_info(self):
         lvl, node, col, it = (ctypes.c_int32() for _ in range(4))

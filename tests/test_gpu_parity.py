@@ -507,3 +507,27 @@ def test_solve_wait_budget_runs_out():
     x_ref = O.solve(O.factor(h), b)
     err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
     assert err.max() <= 1e-10, err
+
+
+# ---------------------------------------------------------------- autotuner
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotuner_choices_and_cache(prec, tmp_path):
+    """hss_tune measures the candidates and keeps the fastest; the object is left
+    factorized with them and still matches the oracle; a second object of the
+    same shape reads the choice from the cache file instead of measuring."""
+    h = I.random_hss(7, 64, 16, seed=70, orthonormal=False)
+    cache = str(tmp_path / "tune.txt")
+    dev = hss.HSS(h)
+    t = dev.tune(prec, nrhs=4, cache=cache)
+    assert t["basis"] in ("householder", "cholqr") and t["schedule"] in ("async", "levels")
+    assert not t["from_cache"] and 0 < t["factor_ms"] < 1e4 and 0 < t["solve_ms"] < 1e4
+    b = I.rhs(h.n, 4, 1)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    x_ref = O.solve(O.factor(h), b)
+    assert (np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)).max() <= 1e-10
+    dev2 = hss.HSS(h)
+    t2 = dev2.tune(prec, nrhs=4, cache=cache)
+    assert t2["from_cache"] and t2["basis"] == t["basis"] and t2["schedule"] == t["schedule"]
+    dev2.factorize(prec, basis="auto", schedule="auto")
+    x2 = dev2.solve(hss.colmajor(b)).cpu().numpy()
+    assert (np.linalg.norm(x2 - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)).max() <= 1e-10
