@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -296,9 +297,10 @@ PEAK_SOURCE = {"pair32": "cuBLAS SGEMM 8192^3 without TF32 (FP32 SIMT) measured 
 
 
 def timed_steps(torch, dev, b, x, prec, steps, clocks=None, residual="fp64", serialize=False):
-    """K timed factor+solve steps on the current stream; returns a dict."""
+    """K timed factor+solve steps on the current stream (basis method, solve
+    schedule and sweep staging as the autotuner chose them); returns a dict."""
     def step():
-        dev.factorize(prec, residual=residual)
+        dev.factorize(prec, residual=residual, basis="auto", schedule="auto")
         dev.solve(b, x)
     torch.cuda.synchronize()
     if clocks:
@@ -319,7 +321,7 @@ def timed_steps(torch, dev, b, x, prec, steps, clocks=None, residual="fp64", ser
     # factor / solve split (one untimed pass)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record()
-    dev.factorize(prec, residual=residual)
+    dev.factorize(prec, residual=residual, basis="auto", schedule="auto")
     e[1].record()
     dev.solve(b, x)
     e[2].record()
@@ -437,8 +439,11 @@ def run_ours(args):
                 / torch.linalg.vector_norm(b, dim=0)).max().item()
 
     resid = args.residual if prec != "fp64" else "fp64"
+    tune_cache = os.environ.get("HSS_TUNE_CACHE") or os.path.join(
+        tempfile.gettempdir(), f"hss_tune_{os.getpid()}.txt")
+    tuning = {prec: dev.tune(prec, w.nrhs, resid, cache=tune_cache)}
     for _ in range(args.warmup):
-        dev.factorize(prec, residual=resid)
+        dev.factorize(prec, residual=resid, basis="auto", schedule="auto")
         dev.solve(b, x)
     if args.profile_step:
         # one step inside the profiler window (ncu --profile-from-start off):
@@ -446,7 +451,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         l0 = dev.launch_count()
-        dev.factorize(prec, residual=resid)
+        dev.factorize(prec, residual=resid, basis="auto", schedule="auto")
         dev.solve(b, x)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
@@ -471,8 +476,9 @@ def run_ours(args):
     ser = timed_steps(torch, dev, b, x, prec, nser, residual=resid, serialize=True)
 
     def variant(p, r_mode):
+        tuning[f"{p}_{r_mode}"] = dev.tune(p, w.nrhs, r_mode, cache=tune_cache)
         for _ in range(2):
-            dev.factorize(p, residual=r_mode)
+            dev.factorize(p, residual=r_mode, basis="auto", schedule="auto")
             dev.solve(b, x)
         g = timed_steps(torch, dev, b, x, p, args.steps, residual=r_mode)
         m = g["ms"] / args.steps
@@ -507,7 +513,7 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, h, w, b_host, prec, fl_step, world, dist)
+        e2e = run_e2e(args, h, w, b_host, prec, fl_step, world, dist, tune_cache)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -550,7 +556,7 @@ def run_ours(args):
                "roofline": roofline_of(ser["trace"], peaks, nser, prec,
                                        overlapped=head["trace"], overlapped_steps=args.steps),
                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
-               "gpu_launches": head["launches"]}
+               "autotune": tuning, "gpu_launches": head["launches"]}
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -621,9 +627,11 @@ def run_batch(args):
     return 0
 
 
-def run_e2e(args, h, w, b_host, prec, fl_step, world, dist):
+def run_e2e(args, h, w, b_host, prec, fl_step, world, dist, tune_cache):
     """One user call sequence per step from pinned host memory: create the object
-    (H2D of the generators), factor, upload b, solve, read x back, destroy."""
+    (H2D of the generators), factor (hss_tune with the cached choice of the
+    autotuner, which factors once with it), upload b, solve, read x back,
+    destroy."""
     import torch
     from paper_2311_00921_gb300 import hss
     import ctypes
@@ -657,8 +665,10 @@ def run_e2e(args, h, w, b_host, prec, fl_step, world, dist):
                                   S.data_ptr(), 0, ctypes.byref(out)), "hss_create")
         st = torch.cuda.current_stream()
         opt = hss.Options(hss.PRECISIONS[prec], 30, 1e-12,
-                          hss.RESIDUALS[args.residual if prec != "fp64" else "fp64"], 0)
-        hss._check(lib.hss_factorize(out, ctypes.byref(opt), st.cuda_stream), "hss_factorize")
+                          hss.RESIDUALS[args.residual if prec != "fp64" else "fp64"],
+                          hss.BASIS_METHODS["auto"], 0, hss.SCHEDULES["auto"], 0)
+        hss._check(lib.hss_tune(out, ctypes.byref(opt), w.nrhs, tune_cache.encode(),
+                                st.cuda_stream, None), "hss_tune")
         bd.copy_(bh, non_blocking=True)
         hss._check(lib.hss_solve(out, bd.data_ptr(), xd.data_ptr(), w.nrhs, w.n, st.cuda_stream),
                    "hss_solve")
@@ -669,7 +679,8 @@ def run_e2e(args, h, w, b_host, prec, fl_step, world, dist):
     return {"value": job_tflops(world, fl_step, 1e3 * dt / steps), "unit": "TFLOP/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": 1e3 * dt / steps, "steps": steps,
-            "includes": "hss_create from pinned host (generators H2D), factorize, b H2D, "
+            "includes": "hss_create from pinned host (generators H2D), factorize (hss_tune with the "
+                        "cached choice), b H2D, "
                         "solve, x D2H, hss_destroy"}
 
 
