@@ -69,6 +69,27 @@ def solve_flops(levels, leaf, r, nrhs):
     return f + 2 * (2 * r) ** 2 * nrhs
 
 
+def tree_flops(h, nrhs):
+    """Canonical factor + solve flops of an HSS matrix on its own node orders
+    and ranks (uneven trees included): leaf i has order b_i and rank r_i, an
+    upper node order r_c1 + r_c2 and its rank, the root order r_1 + r_2."""
+    L = h.levels
+    fl = 0.0
+    for i, b in enumerate(h.sizes):
+        r = int(h.ranks[L][i])
+        fl += node_flops_canonical(int(b), r)
+        c = int(b) - r
+        fl += (4 * b * b + 2 * c * c + 4 * r * c) * nrhs
+    for l in range(L - 1, 0, -1):
+        for i, r in enumerate(h.ranks[l]):
+            b = int(h.ranks[l + 1][2 * i] + h.ranks[l + 1][2 * i + 1])
+            r = int(r)
+            c = b - r
+            fl += node_flops_canonical(b, r) + (4 * b * b + 2 * c * c + 4 * r * c) * nrhs
+    b0 = int(h.ranks[1][0] + h.ranks[1][1])
+    return fl + b0 ** 3 / 3.0 + 2 * b0 * b0 * nrhs
+
+
 # ---------------------------------------------------------------- helpers
 def subtree(h, l0, p):
     """The HSS generators of the subtree under node p of level l0 (the principal
@@ -564,22 +585,23 @@ def run_ours(args):
 
 
 def run_batch(args):
-    """Batched uneven workload: `--batch` matrices of the batched-workload shape
-    distribution (N log-uniform in [4096, 65536] rounded to leaf x 2^L, leaf in
-    {128, 256, 512}, rank in {32, 64, 128}, one right-hand side each), factored
+    """Batched uneven workload: `--batch` matrices of the batched-workload
+    distribution (N log-uniform in [4096, 65536] rounded to a multiple of the
+    leaf size, so the trees are uneven; leaf in {128, 256, 512}, rank in {32,
+    64, 128}; kernel half 1/(d + 1e-3) on the unit cube, half exp(-d/0.1) on a
+    jittered grid, built by the generator; one right-hand side each), factored
     and solved by the batch path (plain and CUDA-graph replay) and by a loop of
-    single-matrix calls.  The generators are random (SPD by a diagonal shift)
-    with those shapes: values do not change the work."""
+    single-matrix calls."""
     import torch
     from paper_2311_00921_gb300 import hss, inputs as I
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     ws = I.batch_workloads(args.batch, seed=1003)
-    mats = [I.random_hss(w.levels, w.leaf, w.rank, seed=w.seed, orthonormal=False,
-                         fast_bound=True) for w in ws]
-    fl = sum(factor_flops(w.levels, w.leaf, w.rank) + solve_flops(w.levels, w.leaf, w.rank, 1)
-             for w in ws)
+    cache = os.environ.get("HSS_INPUT_CACHE")
+    mats = [I.cached_build(w, cache) for w in ws]
     bs = [hss.colmajor(I.rhs(h.n, 1, i)) for i, h in enumerate(mats)]
     out = {}
+    # canonical flops of each tree on its own (uneven) node orders and ranks
+    fl = sum(tree_flops(h, 1) for h in mats)
 
     def timed(fn):
         for _ in range(args.warmup):
@@ -614,9 +636,10 @@ def run_batch(args):
            "value": fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (random generators with the batched workload's shapes)",
+           "data": "synthetic (the generator's cube 1/r and grid exponential kernels)",
            "config": {"workload": f"batch{args.batch}_uneven", "matrices": args.batch,
                       "total_n": int(sum(w.n for w in ws)),
+                      "uneven_trees": int(sum(not h.uniform for h in mats)),
                       "groups": len({(w.leaf, w.rank) for w in ws})},
            "batch_ms": out["batch_ms"], "batch_graph_ms": out["batch_graph_ms"],
            "loop_of_single_calls_ms": out["loop_ms"],

@@ -469,6 +469,10 @@ def cached_build(w: Workload, cache_dir: Optional[str], **kw) -> HSSMatrix:
     key = f"{w.name}_n{w.n}_l{w.leaf}_r{w.rank}_s{w.seed}_{kw.get('mode', 'spd')}.npz"
     path = os.path.join(cache_dir, key.replace("@", "_"))
     L = w.levels
+    if os.path.exists(path[:-4] + ".pkl"):
+        import pickle
+        with open(path[:-4] + ".pkl", "rb") as f:
+            return pickle.load(f)
     if os.path.exists(path):
         z = np.load(path)
         D = list(z["D"])
@@ -479,6 +483,13 @@ def cached_build(w: Workload, cache_dir: Optional[str], **kw) -> HSSMatrix:
         return HSSMatrix(levels=L, sizes=z["sizes"], ranks=ranks, D=D, U=U, E=E, S=S,
                          perm=z["perm"], points=z["points"], workload=w)
     h = build_hss(w, **kw)
+    if not h.uniform:   # uneven trees: pickled (blocks of different shapes)
+        import pickle
+        tmp = path + ".tmp.pkl"
+        with open(tmp, "wb") as f:
+            pickle.dump(h, f)
+        os.replace(tmp, path[:-4] + ".pkl")
+        return h
     if h.uniform:
         arrs = {"D": np.stack(h.D), "U": np.stack(h.U), "sizes": h.sizes, "perm": h.perm,
                 "points": h.points}
@@ -491,20 +502,26 @@ def cached_build(w: Workload, cache_dir: Optional[str], **kw) -> HSSMatrix:
     return h
 
 
-def batch_workloads(count: int, seed: int = 1003, n_min: int = 4096, n_max: int = 65536):
+def batch_workloads(count: int, seed: int = 1003, n_min: int = 4096, n_max: int = 65536,
+                    uniform: bool = False):
     """The batched uneven workload: `count` matrices, N log-uniform in
-    [n_min, n_max] rounded to leaf * 2^L (a uniform tree per matrix), leaf drawn
-    from {128, 256, 512}, rank from {32, 64, 128}, kernel half 1/(d + 1e-3) on
-    the unit cube (+ N^(1/3) I), half exp(-d / 0.1) on a jittered 2-D grid
-    (+ 1e-4 I); one right-hand side each."""
+    [n_min, n_max] rounded to a multiple of the leaf size (so the bisection tree
+    is uneven: L = ceil(log2(N / leaf)), leaf orders in (leaf/2, leaf]; with
+    uniform=True rounded to leaf * 2^L instead), leaf drawn from {128, 256,
+    512}, rank from {32, 64, 128}, kernel half 1/(d + 1e-3) on the unit cube
+    (+ N^(1/3) I), half exp(-d / 0.1) on a jittered 2-D grid (+ 1e-4 I); one
+    right-hand side each."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         leaf = int(rng.choice([128, 256, 512]))
         rank = int(rng.choice([32, 64, 128]))
         n_target = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
-        L = max(1, int(round(math.log2(n_target / leaf))))
-        n = leaf * 2 ** L
+        if uniform:
+            L = max(1, int(round(math.log2(n_target / leaf))))
+            n = leaf * 2 ** L
+        else:
+            n = leaf * max(2, int(round(n_target / leaf)))
         if rng.random() < 0.5:
             w = Workload(f"batch{i}_cube_inv", n, leaf, rank, "cube", "inv", 0.0,
                          round(n ** (1.0 / 3.0), 6), 1, seed * 1000 + i)

@@ -62,9 +62,18 @@ def test_batch_many_groups_and_ragged_shapes():
 
 
 def test_batch_workload_family_reduced():
-    ws = I.batch_workloads(6, seed=7, n_min=512, n_max=4096)
+    ws = I.batch_workloads(6, seed=7, n_min=512, n_max=4096, uniform=True)
     mats = [I.build_hss(w) for w in ws]
     check_batch(mats, 1, 3)
+
+
+def test_batch_workload_family_uneven():
+    """The batched workload as specified: N rounded to a multiple of the leaf
+    size only, so every tree is uneven (padded inside the library)."""
+    ws = I.batch_workloads(6, seed=8, n_min=512, n_max=4096)
+    mats = [I.build_hss(w) for w in ws]
+    assert not any(m.uniform for m in mats)
+    check_batch(mats, 1, 4)
 
 
 def test_batch_graph_replay_matches_plain():
