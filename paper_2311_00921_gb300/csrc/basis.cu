@@ -161,6 +161,162 @@ reverse_basis_kernel(const T* __restrict__ B, long long sB, T* __restrict__ Out,
 
 namespace {
 
+// ---- per-node dense kernels on an r x r block in shared memory (row-major,
+// pitch ld = r + 1), blocked by 32 columns.  Diagonal blocks are factored or
+// inverted by one warp in registers; the rest of each panel step is spread
+// over the CTA with every thread's FMAs independent.
+
+constexpr int NBK = 32;
+constexpr int NWARP = NT / 32;
+
+// element (i, j) of the lower-triangular view: S itself, or its transpose (the
+// upper triangle read as a lower one)
+template <bool TRANS, typename T>
+HSS_DEVINL T& el(T* S, int ld, int i, int j) {
+  return TRANS ? S[j * ld + i] : S[i * ld + j];
+}
+
+// In-place Cholesky S = L Lᵀ of the lower triangle; returns (in every thread)
+// whether a pivot was not positive or not finite (it is then taken as 1).
+template <typename T>
+HSS_DEVINL int chol_blocked(T* S, int ld, int r, int* bad_s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j0 = 0; j0 < r; j0 += NBK) {
+    const int kb = min(NBK, r - j0);
+    if (warp == 0) {   // diagonal block: lane i holds row j0 + i
+      T a[NBK];
+#pragma unroll
+      for (int t = 0; t < NBK; ++t)
+        a[t] = (lane < kb && t < kb && t <= lane) ? S[(j0 + lane) * ld + j0 + t] : T(0);
+      int bad = 0;
+#pragma unroll
+      for (int t = 0; t < NBK; ++t) {
+        T d = __shfl_sync(0xffffffffu, a[t], t);
+        if (t < kb) {
+          if (!(d > T(0)) || !(d <= T(3.0e38))) {
+            bad = 1;
+            d = T(1);
+          }
+          d = sqrt(d);
+          if (lane == t) a[t] = d;
+          if (lane > t) a[t] /= d;
+        }
+#pragma unroll
+        for (int k = t + 1; k < NBK; ++k) {
+          const T xk = __shfl_sync(0xffffffffu, a[t], k);
+          if (t < kb && k < kb && k <= lane) a[k] = fma(-a[t], xk, a[k]);
+        }
+      }
+      if (lane < kb) {
+#pragma unroll
+        for (int t = 0; t < NBK; ++t)
+          if (t < kb && t <= lane) S[(j0 + lane) * ld + j0 + t] = a[t];
+      }
+      if (lane == 0 && bad) *bad_s = 1;
+    }
+    __syncthreads();
+    // rows below: row_i(j0 : j0+kb) L_blk⁻ᵀ, forward substitution per row
+    for (int i = j0 + kb + tid; i < r; i += NT) {
+      T x[NBK];
+#pragma unroll
+      for (int t = 0; t < NBK; ++t) x[t] = t < kb ? S[i * ld + j0 + t] : T(0);
+#pragma unroll
+      for (int t = 0; t < NBK; ++t) {
+        if (t < kb) {
+          x[t] /= S[(j0 + t) * ld + j0 + t];
+#pragma unroll
+          for (int u = t + 1; u < NBK; ++u)
+            if (u < kb) x[u] = fma(-x[t], S[(j0 + u) * ld + j0 + t], x[u]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NBK; ++t)
+        if (t < kb) S[i * ld + j0 + t] = x[t];
+    }
+    __syncthreads();
+    // trailing lower triangle: S(i, k) -= Σ_t L(i, t) L(k, t), k <= i
+    const int m = r - j0 - kb;
+    for (int e = tid; e < m * m; e += NT) {
+      const int i = j0 + kb + e % m, k = j0 + kb + e / m;
+      if (k > i) continue;
+      T s0 = T(0), s1 = T(0);
+      for (int t = 0; t < kb; t += 2) {
+        s0 = fma(S[i * ld + j0 + t], S[k * ld + j0 + t], s0);
+        if (t + 1 < kb) s1 = fma(S[i * ld + j0 + t + 1], S[k * ld + j0 + t + 1], s1);
+      }
+      S[i * ld + k] -= s0 + s1;
+    }
+    __syncthreads();
+  }
+  return *bad_s;
+}
+
+// In-place inverse of the lower-triangular matrix of the view (TRANS: the
+// upper triangle of S read transposed, so its inverse is the inverse of the
+// upper triangle).  UNIT: unit diagonal, implicit and left untouched.
+template <bool TRANS, bool UNIT, typename T>
+HSS_DEVINL void tri_inv_blocked(T* S, int ld, int r) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (r + NBK - 1) / NBK;
+  // diagonal blocks, one warp each: lane j solves L_blk x = e_j
+  for (int p = warp; p < nb; p += NWARP) {
+    const int j0 = p * NBK, kb = min(NBK, r - j0);
+    T x[NBK];
+#pragma unroll
+    for (int t = 0; t < NBK; ++t) x[t] = (t == lane) ? T(1) : T(0);
+#pragma unroll
+    for (int t = 0; t < NBK; ++t) {
+      if (t < kb) {
+        if (!UNIT) x[t] /= el<TRANS>(S, ld, j0 + t, j0 + t);
+#pragma unroll
+        for (int u = t + 1; u < NBK; ++u)
+          if (u < kb) x[u] = fma(-el<TRANS>(S, ld, j0 + u, j0 + t), x[t], x[u]);
+      }
+    }
+    __syncwarp();
+    if (lane < kb) {
+#pragma unroll
+      for (int t = 0; t < NBK; ++t)
+        if (t < kb && (t > lane || (t == lane && !UNIT))) el<TRANS>(S, ld, j0 + t, j0 + lane) = x[t];
+    }
+  }
+  __syncthreads();
+  // block columns right to left: X(i, jb) = -(Σ_{k} Xinv(i, k) X(k, jb)) Xinv_jj
+  for (int jb = nb - 2; jb >= 0; --jb) {
+    const int j0 = jb * NBK;   // a full block (only the last one can be ragged)
+    T acc[NBK];
+    const int i = j0 + NBK + tid;
+    const bool act = i < r;
+    if (act) {
+#pragma unroll
+      for (int t = 0; t < NBK; ++t) acc[t] = T(0);
+      for (int k = j0 + NBK; k <= i; ++k) {
+        const T xik = (UNIT && k == i) ? T(1) : el<TRANS>(S, ld, i, k);
+#pragma unroll
+        for (int t = 0; t < NBK; ++t) acc[t] = fma(xik, el<TRANS>(S, ld, k, j0 + t), acc[t]);
+      }
+    }
+    __syncthreads();
+    if (act) {
+      T out[NBK];
+#pragma unroll
+      for (int u = 0; u < NBK; ++u) {
+        T v = T(0);
+#pragma unroll
+        for (int t = 0; t < NBK; ++t) {
+          if (t < u) continue;   // Xinv_jj lower: t >= u
+          const T w = (UNIT && t == u) ? T(1) : el<TRANS>(S, ld, j0 + t, j0 + u);
+          v = fma(acc[t], w, v);
+        }
+        out[u] = -v;
+      }
+#pragma unroll
+      for (int u = 0; u < NBK; ++u) el<TRANS>(S, ld, i, j0 + u) = out[u];
+    }
+    __syncthreads();
+  }
+}
+
 // One CTA per node: Cholesky G = L Lᵀ of the Gram matrix (lower triangle read,
 // r x r, stride sR) in shared memory, then L⁻¹ in place.  Writes R = Lᵀ and
 // P = L⁻ᵀ = R⁻¹ (both upper, zeros below) and sets fail[node] when a pivot is
@@ -173,7 +329,7 @@ __global__ void __launch_bounds__(NT)
 cholinv_kernel(const T* __restrict__ G, T* __restrict__ Rout, T* __restrict__ Pout, long long sR,
                int r, int* __restrict__ fail, int accumulate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);   // row-major, pitch r + 1
+  T* S = reinterpret_cast<T*>(smem_raw);
   const int ld = r + 1;
   __shared__ int bad;
   const long long node = blockIdx.x;
@@ -188,51 +344,14 @@ cholinv_kernel(const T* __restrict__ G, T* __restrict__ Rout, T* __restrict__ Po
     if (accumulate && i >= j && !(fabs(v - (i == j ? T(1) : T(0))) <= T(0.5))) bad = 1;
   }
   __syncthreads();
-  // right-looking Cholesky, one column per step
-  for (int j = 0; j < r; ++j) {
-    if (tid == 0) {
-      T d = S[j * ld + j];
-      if (!(d > T(0)) || !(d <= T(3.0e38))) {   // not positive, NaN or infinite
-        bad = 1;
-        d = T(1);
-      }
-      S[j * ld + j] = sqrt(d);
-    }
-    __syncthreads();
-    const T inv = T(1) / S[j * ld + j];
-    for (int i = j + 1 + tid; i < r; i += NT) S[i * ld + j] *= inv;
-    __syncthreads();
-    const int m = r - j - 1;
-    for (int e = tid; e < m * m; e += NT) {
-      const int i = j + 1 + e % m, k = j + 1 + e / m;
-      if (k <= i) S[i * ld + k] = fma(-S[i * ld + j], S[k * ld + j], S[i * ld + k]);
-    }
-    __syncthreads();
-  }
+  chol_blocked(S, ld, r, &bad);
   T* Rn = Rout + node * sR;
   for (int e = tid; e < r * r; e += NT) {
     const int i = e % r, j = e / r;
     Rn[e] = (i <= j) ? S[j * ld + i] : T(0);
   }
-  // L⁻¹ in place, columns right to left: column j of the inverse is
-  // -(1 / L(j,j)) L⁻¹(j+1:, j+1:) L(j+1:, j), with column j + 1 .. already inverted
-  for (int j = r - 1; j >= 0; --j) {
-    const T ajj = T(1) / S[j * ld + j];
-    const int i = j + 1 + tid;
-    T v0 = T(0), v1 = T(0);
-    if (i < r) {
-      int k = j + 1;
-      for (; k + 1 <= i; k += 2) {
-        v0 = fma(S[i * ld + k], S[k * ld + j], v0);
-        v1 = fma(S[i * ld + k + 1], S[(k + 1) * ld + j], v1);
-      }
-      if (k <= i) v0 = fma(S[i * ld + k], S[k * ld + j], v0);
-    }
-    __syncthreads();
-    if (i < r) S[i * ld + j] = -ajj * (v0 + v1);
-    if (tid == 0) S[j * ld + j] = ajj;
-    __syncthreads();
-  }
+  __syncthreads();
+  tri_inv_blocked<false, false>(S, ld, r);
   T* Pn = Pout + node * sR;
   for (int e = tid; e < r * r; e += NT) {
     const int i = e % r, j = e / r;
@@ -244,7 +363,8 @@ cholinv_kernel(const T* __restrict__ G, T* __restrict__ Rout, T* __restrict__ Po
 // One CTA per node: the Householder reconstruction of the top r x r block Qt of
 // the orthonormal factor (stride sR; U on exit).  LU without pivoting of
 // Qt - diag(s), s_j = -sign of the running diagonal (+1 for a square basis's
-// last column, where dlarfg leaves the column unreflected); then
+// last column, where dlarfg leaves the column unreflected), blocked by 32
+// columns; then
 //   V(b-1-i, j) = Y1(i, j)            (unit lower, rows b-r .. b-1 of V)
 //   L_B(r-1-i, r-1-j) = s_i R(i, j)   (i <= j; R the Cholesky QR factor)
 //   Ui = U⁻¹, W = S Y1⁻ᵀ              (both upper)
@@ -259,32 +379,92 @@ recon_lu_kernel(T* __restrict__ Qt, T* __restrict__ Ui, T* __restrict__ W,
   __shared__ T sg[256];
   const long long node = blockIdx.x;
   T* q = Qt + node * sR;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < r * r; e += NT) {
     const int i = e % r, j = e / r;
     S[i * ld + j] = q[e];
   }
   __syncthreads();
-  for (int j = 0; j < r; ++j) {
-    if (tid == 0) {
-      const T u = S[j * ld + j];
-      T s = u >= T(0) ? T(-1) : T(1);
-      if (b == r && j == r - 1) s = u >= T(0) ? T(1) : T(-1);
-      sg[j] = s;
-      S[j * ld + j] = (b == r && j == r - 1) ? T(0) : u - s;
+  for (int j0 = 0; j0 < r; j0 += NBK) {
+    const int kb = min(NBK, r - j0);
+    if (warp == 0) {   // diagonal block LU with the sign rule: lane i holds row j0 + i
+      T a[NBK];
+#pragma unroll
+      for (int t = 0; t < NBK; ++t) a[t] = (lane < kb && t < kb) ? S[(j0 + lane) * ld + j0 + t] : T(0);
+#pragma unroll
+      for (int t = 0; t < NBK; ++t) {
+        const T u = __shfl_sync(0xffffffffu, a[t], t);
+        if (t < kb) {
+          const bool last_sq = (b == r && j0 + t == r - 1);
+          T s = u >= T(0) ? T(-1) : T(1);
+          if (last_sq) s = -s;
+          const T piv = last_sq ? T(0) : u - s;
+          if (lane == 0) sg[j0 + t] = s;
+          if (lane == t) a[t] = piv;
+          if (lane > t) a[t] /= piv;
+        }
+#pragma unroll
+        for (int k = t + 1; k < NBK; ++k) {
+          const T ukt = __shfl_sync(0xffffffffu, a[k], t);
+          if (t < kb && k < kb && lane > t) a[k] = fma(-a[t], ukt, a[k]);
+        }
+      }
+      if (lane < kb) {
+#pragma unroll
+        for (int t = 0; t < NBK; ++t)
+          if (t < kb) S[(j0 + lane) * ld + j0 + t] = a[t];
+      }
     }
     __syncthreads();
-    const int m = r - j - 1;
-    if (m > 0) {
-      const T inv = T(1) / S[j * ld + j];
-      for (int i = j + 1 + tid; i < r; i += NT) S[i * ld + j] *= inv;
-      __syncthreads();
-      for (int e = tid; e < m * m; e += NT) {
-        const int i = j + 1 + e % m, k = j + 1 + e / m;
-        S[i * ld + k] = fma(-S[i * ld + j], S[j * ld + k], S[i * ld + k]);
+    const int m = r - j0 - kb;
+    // L panel rows (A U_blk⁻¹, row-wise) and U panel columns (L_blk⁻¹ A, unit lower)
+    for (int task = tid; task < 2 * m; task += NT) {
+      T x[NBK];
+      if (task < m) {
+        const int i = j0 + kb + task;
+#pragma unroll
+        for (int t = 0; t < NBK; ++t) x[t] = t < kb ? S[i * ld + j0 + t] : T(0);
+#pragma unroll
+        for (int t = 0; t < NBK; ++t) {
+          if (t < kb) {
+            x[t] /= S[(j0 + t) * ld + j0 + t];
+#pragma unroll
+            for (int u2 = t + 1; u2 < NBK; ++u2)
+              if (u2 < kb) x[u2] = fma(-x[t], S[(j0 + t) * ld + j0 + u2], x[u2]);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < NBK; ++t)
+          if (t < kb) S[i * ld + j0 + t] = x[t];
+      } else {
+        const int k = j0 + kb + (task - m);
+#pragma unroll
+        for (int t = 0; t < NBK; ++t) x[t] = t < kb ? S[(j0 + t) * ld + k] : T(0);
+#pragma unroll
+        for (int t = 0; t < NBK; ++t) {
+          if (t < kb) {
+#pragma unroll
+            for (int u2 = t + 1; u2 < NBK; ++u2)
+              if (u2 < kb) x[u2] = fma(-S[(j0 + u2) * ld + j0 + t], x[t], x[u2]);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < NBK; ++t)
+          if (t < kb) S[(j0 + t) * ld + k] = x[t];
       }
-      __syncthreads();
     }
+    __syncthreads();
+    // trailing square: S(i, k) -= Σ_t L(i, t) U(t, k)
+    for (int e = tid; e < m * m; e += NT) {
+      const int i = j0 + kb + e % m, k = j0 + kb + e / m;
+      T s0 = T(0), s1 = T(0);
+      for (int t = 0; t < kb; t += 2) {
+        s0 = fma(S[i * ld + j0 + t], S[(j0 + t) * ld + k], s0);
+        if (t + 1 < kb) s1 = fma(S[i * ld + j0 + t + 1], S[(j0 + t + 1) * ld + k], s1);
+      }
+      S[i * ld + k] -= s0 + s1;
+    }
+    __syncthreads();
   }
   T* Vn = V + node * sV;
   T* Ln = LB + node * sL;
@@ -297,42 +477,8 @@ recon_lu_kernel(T* __restrict__ Qt, T* __restrict__ Ui, T* __restrict__ W,
     Ln[(r - 1 - i) + (long long)(r - 1 - j) * r] = i <= j ? sg[i] * Rn[e] : T(0);
   }
   __syncthreads();
-  // U⁻¹ in place (upper triangle with the diagonal), columns left to right
-  for (int j = 0; j < r; ++j) {
-    const T ujj = S[j * ld + j];
-    const int i = tid;
-    T v0 = T(0), v1 = T(0);
-    if (i < j) {
-      int k = i;
-      for (; k + 1 < j; k += 2) {
-        v0 = fma(S[i * ld + k], S[k * ld + j], v0);
-        v1 = fma(S[i * ld + k + 1], S[(k + 1) * ld + j], v1);
-      }
-      if (k < j) v0 = fma(S[i * ld + k], S[k * ld + j], v0);
-    }
-    __syncthreads();
-    const T inv = T(1) / ujj;
-    if (i < j) S[i * ld + j] = -(v0 + v1) * inv;
-    if (tid == 0) S[j * ld + j] = inv;
-    __syncthreads();
-  }
-  // Y1⁻¹ in place (strictly lower, unit diagonal implicit), columns right to left
-  for (int j = r - 2; j >= 0; --j) {
-    const int i = j + 1 + tid;
-    T v0 = T(0), v1 = T(0);
-    if (i < r) {
-      v0 = S[i * ld + j];
-      int k = j + 1;
-      for (; k + 1 < i; k += 2) {
-        v0 = fma(S[i * ld + k], S[k * ld + j], v0);
-        v1 = fma(S[i * ld + k + 1], S[(k + 1) * ld + j], v1);
-      }
-      if (k < i) v0 = fma(S[i * ld + k], S[k * ld + j], v0);
-    }
-    __syncthreads();
-    if (i < r) S[i * ld + j] = -(v0 + v1);
-    __syncthreads();
-  }
+  tri_inv_blocked<true, false>(S, ld, r);   // U⁻¹ (upper triangle with the diagonal)
+  tri_inv_blocked<false, true>(S, ld, r);   // Y1⁻¹ (strictly lower, unit diagonal)
   T* Un = Ui + node * sR;
   T* Wn = W + node * sR;
   for (int e = tid; e < r * r; e += NT) {
