@@ -335,12 +335,21 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < M) {
+        // C_in may be C itself: each element is read and written by this thread
+        // only, so the 32 reads go out together before any write
+        float ci[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          const bool ok = cin && col < N && !(lower_only && col > row);
+          ci[j] = ok ? cin[row + (long long)col * ldcin] : 0.f;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + c0 + j;
           if (col >= N || (lower_only && col > row)) continue;
           float out = alpha * __uint_as_float(v[j]);
-          if (cin) out = fmaf(beta, cin[row + (long long)col * ldcin], out);
+          if (cin) out = fmaf(beta, ci[j], out);
           c[row + (long long)col * ldc] = out;
         }
       }
