@@ -302,15 +302,16 @@ gemm_n16_small_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int
 
 // n <= 16 columns on few nodes: the products at the top of the tree, where a
 // launch has only a handful of CTAs and a tile loop leaves each SM's pipe idle
-// between dependent steps.  Both kernels keep every thread's FMAs independent
-// and sum in a fixed order.
-// op(A) = A: CTA = 32 rows of one node (lane = row, loads coalesced); warp w
-// accumulates K slice w of 8 for all n columns, the slices are added in order.
-template <typename T, bool BETA>
+// between dependent steps.  CTA = 32 output rows of one node, lane = row; warp
+// w accumulates K slice w of 8 for all n columns (the right-hand block is one
+// broadcast read for the 32 rows), and the slices are added in a fixed order.
+// TA: op(A) = Aᵀ, each lane walks its own row of Aᵀ (a column of A) through
+// L1-resident lines; else the 32 lanes read one column of A, coalesced.
+template <typename T, bool TA, bool BETA>
 __global__ void __launch_bounds__(256)
-gemm_lat_n_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, long long sA,
-                  const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
-                  long long sC) {
+gemm_lat_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, long long sA,
+                const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
+                long long sC) {
   __shared__ T part[8][32][17];
   const long long bz = blockIdx.y;
   A += bz * sA;
@@ -324,7 +325,7 @@ gemm_lat_n_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda
   for (int j = 0; j < 16; ++j) acc[j] = T(0);
   if (i < m) {
     for (int kk = k0; kk < k1; ++kk) {
-      const T a = A[i + (long long)kk * lda];
+      const T a = TA ? A[kk + (long long)i * lda] : A[i + (long long)kk * lda];
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         if (j < n) acc[j] = fma(a, B[kk + (long long)j * ldb], acc[j]);
@@ -342,41 +343,6 @@ gemm_lat_n_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda
     for (int q = 0; q < 8; ++q) s += part[q][rr][j];
     T* c = C + gi + (long long)j * ldc;
     *c = BETA ? fma(alpha, s, beta * *c) : alpha * s;
-  }
-}
-
-// op(A) = Aᵀ: warp = one output row (all n columns); the lanes split K
-// (loads of the row of Aᵀ coalesced), then a butterfly sum per column.
-template <typename T, bool BETA>
-__global__ void __launch_bounds__(256)
-gemm_lat_t_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, long long sA,
-                  const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
-                  long long sC) {
-  const long long bz = blockIdx.y;
-  A += bz * sA;
-  B += bz * sB;
-  C += bz * sC;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * 8 + w;
-  if (i >= m) return;   // warp-uniform
-  T acc[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j] = T(0);
-  for (int kk = lane; kk < k; kk += 32) {
-    const T a = A[kk + (long long)i * lda];
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < n) acc[j] = fma(a, B[kk + (long long)j * ldb], acc[j]);
-  }
-  T out = T(0);
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const T s = warp_sum(acc[j]);
-    if (lane == j) out = s;
-  }
-  if (lane < n) {
-    T* c = C + i + (long long)lane * ldc;
-    *c = BETA ? fma(alpha, out, beta * *c) : alpha * out;
   }
 }
 
@@ -503,24 +469,14 @@ void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA
                  cudaStream_t st) {
   const bool useb = beta != T(0);
   if (!TB && n <= 16 && (long long)((m + 127) / 128) * batch < 152 && batch <= 65535) {
-    // few nodes: the low-latency kernels
-    if (!TA) {
-      dim3 g((m + 31) / 32, batch);
-      if (useb)
-        gemm_lat_n_kernel<T, true><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta,
+    // few nodes: the low-latency kernel
+    dim3 g((m + 31) / 32, batch);
+    if (useb)
+      gemm_lat_kernel<T, TA, true><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta,
                                                        C, ldc, sC);
-      else
-        gemm_lat_n_kernel<T, false><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
+    else
+      gemm_lat_kernel<T, TA, false><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
                                                         beta, C, ldc, sC);
-    } else {
-      dim3 g((m + 7) / 8, batch);
-      if (useb)
-        gemm_lat_t_kernel<T, true><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta,
-                                                       C, ldc, sC);
-      else
-        gemm_lat_t_kernel<T, false><<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
-                                                        beta, C, ldc, sC);
-    }
     return;
   }
   if (n > 4 && n <= 16 && (long long)((m + 127) / 128) * batch < 152) {
