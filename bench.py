@@ -650,6 +650,66 @@ def run_batch(args):
     return 0
 
 
+def run_sweep(args):
+    """The paper's two scaling experiments on one GPU (Sec. 5: problem size with
+    constant resources, and the impact of the leaf size): factor + solve time of
+    the FP64 path and of the headline mixed path (FP32 factor, FP64-residual
+    refinement to 1e-12) over N = 2^14 .. 2^18 at leaf 512 / rank 128, and over
+    leaf sizes 128 .. 768 at N = 2^17 with rank 96 (the paper's leaf study uses
+    rank 100).  16 right-hand sides.  Random generators with these shapes (SPD
+    by a diagonal shift): the values do not change the work.  One JSON line per
+    point, then a summary line."""
+    import torch
+    from paper_2311_00921_gb300 import hss, inputs as I
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nrhs = 16
+    points = [("n", 2 ** k, 512, 128) for k in range(14, 19)]
+    points += [("leaf", 2 ** 17, leaf, 96) for leaf in (128, 192, 256, 384, 512, 768)]
+    out = []
+    for kind, n, leaf, r in points:
+        L = int(round(math.log2(n / leaf)))
+        if leaf * 2 ** L != n:
+            L = int(math.ceil(math.log2(n / leaf)))
+        h = I.random_hss(L, leaf, r, seed=L * 1000 + leaf, orthonormal=False, fast_bound=True)
+        dev = hss.HSS(h)
+        b = hss.colmajor(I.rhs(h.n, nrhs, 1))
+        x = torch.empty_like(b)
+        rec = {"sweep": kind, "n": h.n, "leaf": leaf, "rank": r, "levels": L}
+        fl = factor_flops(L, leaf, r) + solve_flops(L, leaf, r, nrhs)
+        for prec in ("fp64", "fp32"):
+            dev.tune(prec, nrhs, "fp64")
+            for _ in range(args.warmup):
+                dev.factorize(prec, basis="auto", schedule="auto")
+                dev.solve(b, x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                dev.factorize(prec, basis="auto", schedule="auto")
+                dev.solve(b, x)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            rec[prec] = {"ms_per_step": ms, "tflops": fl / (ms / 1e3) / 1e12}
+        rec["mixed_speedup"] = rec["fp64"]["ms_per_step"] / rec["fp32"]["ms_per_step"]
+        print(json.dumps(rec), flush=True)
+        out.append(rec)
+        del dev
+        torch.cuda.empty_cache()
+    nrec = [r for r in out if r["sweep"] == "n"]
+    # growth of the time per unknown from the smallest to the largest N (1.0 = O(N))
+    growth = {p: (nrec[-1][p]["ms_per_step"] / nrec[-1]["n"]) /
+                 (nrec[0][p]["ms_per_step"] / nrec[0]["n"]) for p in ("fp64", "fp32")}
+    print(json.dumps({"metric": "HSS-ULV factor+solve time vs N and leaf size (1 GPU)",
+                      "points": len(out), "time_per_unknown_growth_n14_to_n18": growth,
+                      "best_leaf_fp32": min((r for r in out if r["sweep"] == "leaf"),
+                                            key=lambda r: r["fp32"]["ms_per_step"])["leaf"],
+                      "best_leaf_fp64": min((r for r in out if r["sweep"] == "leaf"),
+                                            key=lambda r: r["fp64"]["ms_per_step"])["leaf"]}),
+          flush=True)
+    return 0
+
+
 def run_e2e(args, h, w, b_host, prec, fl_step, world, dist, tune_cache):
     """One user call sequence per step from pinned host memory: create the object
     (H2D of the generators), factor (hss_tune with the cached choice of the
@@ -724,6 +784,8 @@ def main():
                          "(for ncu --profile-from-start off) and exit")
     ap.add_argument("--cpu-full", action="store_true",
                     help="also time the oracle once on the whole matrix (about 100 s at N=2^18)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time the FP64 and mixed paths over N and over the leaf size instead")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched uneven workload with this many matrices instead")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -738,6 +800,8 @@ def main():
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -76,8 +76,8 @@ typedef enum {
 
 typedef struct {
   int32_t n;      /* matrix order: leaf * 2^levels, or the sum of node_sizes */
-  int32_t leaf;   /* leaf block order (1 .. 768; FP64 solves: see hss_solve); with
-                     node_sizes, the largest leaf order */
+  int32_t leaf;   /* leaf block order (1 .. 768); with node_sizes, the largest leaf
+                     order */
   int32_t rank;   /* rank of every basis (1 .. min(leaf, 256)); with node_sizes the
                      largest rank, see below */
   int32_t levels; /* L >= 1 */
@@ -181,9 +181,8 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream);
  * matvec in the arithmetic hss_options.residual selects) and synchronizes once per
  * iteration; it returns HSS_ERR_NO_CONVERGENCE if ir_max_it is reached (x then
  * holds the last iterate).  Errors: NOT_FACTORIZED, INVALID_ARG, CUDA.
- * Shared memory bounds one level's sweep: with an FP64 factor and 16 columns per
- * pass (nrhs >= 16) the leaf order must be <= 617, else INVALID_ARG (fewer
- * columns allow larger leaves; FP32 factors allow every leaf up to 768). */
+ * Every leaf order up to 768 is solved in every precision (the sweeps stage their
+ * panels in as much shared memory as the device grants). */
 int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, void* stream);
 
 /* log det A from the factorized form (Eq. hss-ulv-final-form): twice the sum of

@@ -698,7 +698,8 @@ constexpr int ZP = 17;
 // t1, t2 hold r x 16 row by row, zp NT x ZP partial sums.  The products read a
 // row of 16 right-hand sides with 128-bit loads that every lane shares, so
 // each FMA costs about a third of a shared load.  Called by every thread with
-// y visible; returns with no copy in flight.
+// y visible; returns with no copy in flight.  y = null: the vector lives only
+// in yr (row by row), and the update goes there.
 template <typename T>
 HSS_DEVINL void q_apply(T* y, T* yr, bool fill, int b, int nrhs, const T* V, const T* Tm, int r,
                         bool transpose, T* Lbuf, int P, int CB, int NBUF, T* zp, T* t1, T* t2) {
@@ -783,7 +784,12 @@ HSS_DEVINL void q_apply(T* y, T* yr, bool fill, int b, int nrhs, const T* V, con
           }
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (j < nrhs) y[i + j * b] -= a[j];
+            if (j < nrhs) {
+              if (y)
+                y[i + j * b] -= a[j];
+              else
+                yr[i * 16 + j] -= a[j];
+            }
         }
       }
       __syncthreads();
@@ -934,14 +940,14 @@ HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
                          long long sPar, const T* Vb, long long sV, const T* Tb, long long sT,
                          int r, int CB, int NBUF) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs
-  const int P = b | 1;
-  // b x 16 row-major shadow of the solved rows (16-byte aligned for vector loads)
-  T* xt = y + (((size_t)b * nrhs + 15) & ~size_t(15));
+  // the node vector row by row (pitch 16, zero past nrhs; 16-byte aligned for
+  // vector loads): the only copy of it in shared memory
+  T* xt = reinterpret_cast<T*>(smem_raw);
   T* zp = xt + (size_t)b * 16;             // NT x ZP partial sums
   T* t1 = zp + (size_t)NT * ZP;
   T* t2 = t1 + (size_t)16 * (Vb ? r : 0);
   T* Lbuf = t2 + (size_t)16 * (Vb ? r : 0);
+  const int P = b | 1;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
@@ -951,20 +957,17 @@ HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
     stage_panel(M, ldm, k0, c - k0, b, Lbuf + (size_t)(NBUF == 2 ? ((nblk - 1) & 1) : 0) * P * CB,
                 P);
   }
-  for (int e = tid; e < b * nrhs; e += NT) {
+  // x^S (rows c .. b-1) from the parent's vector, z^R from this level's
+  for (int e = tid; e < b * 16; e += NT) {
     const int i = e % b, j = e / b;
-    T v;
-    if (i >= c && Par)
-      v = ldv<CG>(Par + (long long)node * sPar + (i - c) + (long long)j * ldpar);
-    else
-      v = ldv<CG>(x + i + (long long)j * ldx);
-    y[i + j * b] = v;
-  }
-  __syncthreads();
-  // rows c .. b-1 (x^S) are final from the start
-  for (int e = tid; e < (b - c) * 16; e += NT) {
-    const int i = c + e / 16, j = e % 16;
-    xt[i * 16 + j] = j < nrhs ? y[i + j * b] : T(0);
+    T v = T(0);
+    if (j < nrhs) {
+      if (i >= c && Par)
+        v = ldv<CG>(Par + (long long)node * sPar + (i - c) + (long long)j * ldpar);
+      else
+        v = ldv<CG>(x + i + (long long)j * ldx);
+    }
+    xt[i * 16 + j] = v;
   }
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int k0 = bi * CB;
@@ -979,8 +982,7 @@ HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
     }
     __syncthreads();
     // z_t -= Σ_{i >= k0+kb} L(i, t) x_i: thread (t = lane, rows i ≡ warp mod nw)
-    // accumulates every right-hand side from the row-major shadow, then the
-    // warps' partial sums are added
+    // accumulates every right-hand side, then the warps' partial sums are added
     {
       T acc[16];
 #pragma unroll
@@ -1004,7 +1006,7 @@ HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
         T sum = T(0);
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w) sum += zp[(w * NB + t) * ZP + j];
-        y[(k0 + t) + j * b] -= sum;
+        xt[(k0 + t) * 16 + j] -= sum;
       }
     }
     __syncthreads();
@@ -1017,35 +1019,30 @@ HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
         lcol[t] = (lane < kb && t >= lane && t < kb) ? L[t + lane * P] : T(0);
       const T inv = lane < kb ? T(1) / reg_select(lcol, lane) : T(0);
       for (int j = wid; j < nrhs; j += nw) {
-        T* yj = y + j * b + k0;
-        T v = lane < kb ? yj[lane] : T(0);
+        T v = lane < kb ? xt[(k0 + lane) * 16 + j] : T(0);
 #pragma unroll
         for (int tt = NB - 1; tt >= 0; --tt) {
           if (tt >= kb) continue;
           if (lane == tt) v *= inv;
-          const T xt = __shfl_sync(0xffffffffu, v, tt);
-          if (lane < tt) v = fma(-lcol[tt], xt, v);
+          const T xs = __shfl_sync(0xffffffffu, v, tt);
+          if (lane < tt) v = fma(-lcol[tt], xs, v);
         }
-        if (lane < kb) yj[lane] = v;
+        if (lane < kb) xt[(k0 + lane) * 16 + j] = v;
       }
     }
     __syncthreads();
-    for (int e = tid; e < kb * 16; e += NT) {   // the block's rows are final now
-      const int i = k0 + e / 16, j = e % 16;
-      xt[i * 16 + j] = j < nrhs ? y[i + j * b] : T(0);
-    }
     if (NBUF == 1 && next) stage_panel(M, ldm, k0 - CB, CB, b, Lbuf, P);
   }
   cp_async_wait<0>();
-  if (Vb) {   // y := Q y
+  if (Vb) {   // x := Q x, on the row-major vector
     __syncthreads();
-    q_apply(y, xt, false, b, nrhs, Vb + (long long)node * sV, Tb + (long long)node * sT, r, false,
-            Lbuf, P, CB, NBUF, zp, t1, t2);
+    q_apply<T>(nullptr, xt, false, b, nrhs, Vb + (long long)node * sV, Tb + (long long)node * sT,
+               r, false, Lbuf, P, CB, NBUF, zp, t1, t2);
   }
   __syncthreads();
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
-    x[i + (long long)j * ldx] = y[i + j * b];
+    x[i + (long long)j * ldx] = xt[i * 16 + j];
   }
 }
 
@@ -1274,9 +1271,10 @@ cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T
 // buffers, and NBUF staged panels of P x CB
 template <typename T>
 size_t trsv_smem(int b, int nrhs, int r, int CB, int NBUF, bool bwd) {
-  // the node vector (padded to 16 elements); the row-major shadow and partial
-  // sums (backward sweep, or any Q application); t1, t2; the panels
-  const size_t vec = ((size_t)b * nrhs + 15) & ~size_t(15);
+  // forward: the column-major vector (padded to 16 elements), plus its row-major
+  // copy and the partial sums when Q is applied; backward: the row-major vector
+  // and the partial sums only
+  const size_t vec = bwd ? 0 : ((size_t)b * nrhs + 15) & ~size_t(15);
   const size_t rowmajor = (bwd || r > 0) ? (size_t)b * 16 + (size_t)NT * ZP : 0;
   return (vec + rowmajor + (size_t)32 * r + (size_t)NBUF * (b | 1) * CB) * sizeof(T);
 }

@@ -531,3 +531,21 @@ def test_autotuner_choices_and_cache(prec, tmp_path):
     dev2.factorize(prec, basis="auto", schedule="auto")
     x2 = dev2.solve(hss.colmajor(b)).cpu().numpy()
     assert (np.linalg.norm(x2 - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)).max() <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_leaf_768_sixteen_columns(prec):
+    """The largest leaf order with 16 right-hand sides per pass in FP64 (the
+    backward sweep keeps only the row-major vector in shared memory, so the
+    panels fit), against the oracle."""
+    h = I.random_hss(2, 768, 96, seed=768, orthonormal=False)
+    dev = hss.HSS(h)
+    dev.factorize(prec)
+    b = I.rhs(h.n, 16, 3)
+    x = dev.solve(hss.colmajor(b)).cpu().numpy()
+    F = O.factor(h)
+    x_ref = O.solve(F, b)
+    err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+    assert err.max() <= 1e-10, err
+    if prec == "fp64":
+        check_end_to_end(dev, F, b, x)
