@@ -250,6 +250,8 @@ typedef struct {
   int32_t from_cache; /* 1 when read from the cache file instead of measured */
   double factor_ms;   /* one factorization with the chosen basis method */
   double solve_ms;    /* one solve of min(nrhs, 16) columns with the chosen schedule */
+  double factor_ms_by_basis[2];        /* every candidate measured: [basis method] */
+  double solve_ms_by_config[2][2];     /* [schedule][staging]; 0 where not measured */
 } hss_tuning;
 
 /* Autotuner: for the object's shape and the arithmetic of opt (precision,

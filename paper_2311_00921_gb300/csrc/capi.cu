@@ -1306,6 +1306,7 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
       o.schedule = HSS_SCHEDULE_ASYNC;
       double ms = 0.0;
       rc = timed([&] { return hss_factorize(h, &o, st); }, &ms);
+      if (rc == HSS_OK) best.factor_ms_by_basis[basis] = ms;
       if (rc == HSS_OK && ms < best.factor_ms) {
         best.factor_ms = ms;
         best.basis = basis;
@@ -1322,6 +1323,7 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
         h->staging = stg;
         double ms = 0.0;
         rc = timed([&] { return hss_solve(h, b, x, nc, h->n_user, st); }, &ms);
+        if (rc == HSS_OK) best.solve_ms_by_config[sched][stg] = ms;
         if (rc == HSS_OK && ms < best.solve_ms) {
           best.solve_ms = ms;
           best.schedule = sched;

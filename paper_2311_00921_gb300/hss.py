@@ -45,7 +45,9 @@ SCHEDULES = {"async": 0, "levels": 1, "auto": 2}
 class Tuning(ctypes.Structure):
     _fields_ = [("basis", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("staging", ctypes.c_int32), ("from_cache", ctypes.c_int32),
-                ("factor_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("factor_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("factor_ms_by_basis", ctypes.c_double * 2),
+                ("solve_ms_by_config", (ctypes.c_double * 2) * 2)]
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -284,7 +286,13 @@ class HSS:
         return {"basis": names_b[t.basis], "schedule": names_s[t.schedule],
                 "staging": "fewest_waves" if t.staging else "largest_panels",
                 "from_cache": bool(t.from_cache), "factor_ms": t.factor_ms,
-                "solve_ms": t.solve_ms}
+                "solve_ms": t.solve_ms,
+                "measured": None if t.from_cache else {
+                    "factor_ms": {names_b[k]: t.factor_ms_by_basis[k] for k in range(2)
+                                  if t.factor_ms_by_basis[k] > 0},
+                    "solve_ms": {f"{names_s[s]}/{'fewest_waves' if g else 'largest_panels'}":
+                                 t.solve_ms_by_config[s][g] for s in range(2) for g in range(2)
+                                 if t.solve_ms_by_config[s][g] > 0}}}
 
     def last_info(self):
         lvl, node, col, it = (ctypes.c_int32() for _ in range(4))
