@@ -60,6 +60,19 @@ struct Factor {
   size_t bytes = 0;
 };
 
+// One refinement lane: the right-hand-side columns [col0, col0 + nc) of a pass
+// refine on their own stream with their own slice of every scratch vector, so
+// that two lanes overlap (one lane's FP32 sweeps beside the other's FP64
+// matvec).  Lane 0 runs on the caller's stream.
+struct Lane {
+  cudaStream_t st = nullptr;        // lane 1 only (lane 0 uses the caller's)
+  cudaStream_t ms = nullptr;        // the matvec's leaf product D x
+  cudaEvent_t mv_start = nullptr, mv_dx = nullptr, norm_ready = nullptr;
+  int* tcnt = nullptr;              // arrival counts of the tree forward sweep
+  int* tready = nullptr;            // ready flags of the tree backward sweep
+  int epoch = 0;
+};
+
 }  // namespace
 
 struct hss_s {
@@ -104,9 +117,7 @@ struct hss_s {
   int staging = 0;                     // panel staging of the sweep kernels (see launch_ulv_fwd)
   int tuned = 0;                       // hss_tune has chosen the following
   int tuned_basis = HSS_BASIS_HOUSEHOLDER, tuned_schedule = HSS_SCHEDULE_ASYNC, tuned_staging = 0;
-  int* tree_cnt = nullptr;             // arrival counts of the tree forward sweep
-  int* tree_ready = nullptr;           // ready flags of the tree backward sweep
-  int tree_epoch = 0;
+
   // pair-of-FP32 generators (hi parts are the FP32 factor's converted copies)
   // and the pair matvec's vectors, in the FP32 arena
   float *Dl = nullptr, *Ul = nullptr, *El = nullptr, *Sl = nullptr;
@@ -118,9 +129,11 @@ struct hss_s {
   cudaStream_t qstream = nullptr;
   std::vector<cudaEvent_t> ev_level;
   cudaEvent_t ev_start = nullptr;
-  // the FP64 matvec's leaf product D x runs on its own stream beside the sweeps
-  cudaStream_t mstream = nullptr;
-  cudaEvent_t ev_mv_start = nullptr, ev_mv_dx = nullptr;
+  Lane lane[2];                        // refinement lanes (lane 0 also serves every other call)
+  cudaEvent_t ev_ir_fork = nullptr, ev_ir_join = nullptr;
+  double* hnorm = nullptr;             // pinned host: |b|, |r| of the kSolveCols columns, then
+                                       // each refinement lane's status words (8 ints a lane)
+  int ir_lanes = 2;                    // 1: one lane (no overlap)
   double* zq64 = nullptr;              // merge scratch of the basis chain (n_L/2 x r x r)
   float* zq32 = nullptr;
   int ir_iters = 0;
@@ -128,7 +141,8 @@ struct hss_s {
   // launch accounting and the optional per-launch event log
   long long launches = 0;
   int tracing = 0;
-  int serialize = 0;                   // run the basis chain on the caller's stream
+  int serialize = 0;                   // run the basis chain, the matvec and the
+                                       // refinement on the caller's stream only
   struct Rec {
     int kind;
     double flops;
@@ -231,8 +245,10 @@ size_t layout_main(hss_s* h, char* base) {
   h->logdet_part = bp.take<double>((size_t)(2 * nL - 1) + kRootPanels);
   h->logdet_val = bp.take<double>(1);
   h->status = bp.take<int>(8);
-  h->tree_cnt = bp.take<int>(size_t(2) << kTreeTop);
-  h->tree_ready = bp.take<int>(size_t(2) << kTreeTop);
+  for (Lane& ln : h->lane) {
+    ln.tcnt = bp.take<int>(size_t(2) << kTreeTop);
+    ln.tready = bp.take<int>(size_t(2) << kTreeTop);
+  }
   if (h->uneven) {
     h->pmap = bp.take<int>((size_t)h->n);
     h->vin = bp.take<double>((size_t)h->n * kMaxCols);
@@ -613,20 +629,29 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
 // three batched GEMMs over the level (used where the level has many nodes)
 template <typename T>
 void apply_q(hss_s* h, Factor<T>& f, const LevelT<T>& P, T* vec, int ldv, int nc, bool transpose,
-             cudaStream_t st) {
+             cudaStream_t st, int col0) {
   const int b = P.b, r = P.r, n = P.n;
   const long long s1 = (long long)r * kSolveCols;
-  gemm<T>(h, true, false, r, nc, b, T(1), P.V, b, (long long)b * r, vec, ldv, b, T(0), f.t1, r, s1,
+  T* t1 = f.t1 + (long long)col0 * r;   // this lane's columns of the scratch
+  T* t2 = f.t2 + (long long)col0 * r;
+  gemm<T>(h, true, false, r, nc, b, T(1), P.V, b, (long long)b * r, vec, ldv, b, T(0), t1, r, s1,
           n, st);
-  gemm<T>(h, transpose, false, r, nc, r, T(1), P.T_, r, (long long)r * r, f.t1, r, s1, T(0), f.t2,
-          r, s1, n, st);
-  gemm<T>(h, false, false, b, nc, r, T(-1), P.V, b, (long long)b * r, f.t2, r, s1, T(1), vec, ldv,
+  gemm<T>(h, transpose, false, r, nc, r, T(1), P.T_, r, (long long)r * r, t1, r, s1, T(0), t2, r,
+          s1, n, st);
+  gemm<T>(h, false, false, b, nc, r, T(-1), P.V, b, (long long)b * r, t2, r, s1, T(1), vec, ldv,
           b, n, st);
 }
 
+// The ULV sweeps on nc <= kSolveCols columns of x (in place), arithmetic T;
+// the root solve is FP64 in every mode.  Lane g uses columns col0 .. col0+nc-1
+// of every level vector and scratch block, and its own tree flags.
 template <typename T>
-int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) {
+int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st, int g = 0,
+                 int col0 = 0) {
   const int L = h->L, r = h->rank;
+  Lane& ln = h->lane[g];
+  // level l's vector, this lane's columns
+  auto lvec = [&](int l) { return f.lv[l].yv + (long long)col0 * f.lv[l].n * f.lv[l].b; };
   // levels lo .. 1 (the narrow top of the tree) run as one launch per direction
   const int lo = h->schedule == HSS_SCHEDULE_ASYNC ? std::min(L - 1, kTreeTop) : 0;
   TreeLevels<T> tl{};
@@ -635,46 +660,48 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
     tl.M[l] = f.lv[l].M;
     tl.V[l] = f.lv[l].V;
     tl.Tm[l] = f.lv[l].T_;
-    tl.vec[l] = f.lv[l].yv;
+    tl.vec[l] = lvec(l);
     if (l >= 1) tree_flops += (trsv_flops(2 * r, r, nc) + qapply_flops(2 * r, r, nc)) * (1 << l);
   }
   for (int l = L; l > lo; --l) {
     LevelT<T>& P = f.lv[l];
     LevelT<T>& Q = f.lv[l - 1];
-    T* vec = (l == L) ? x : P.yv;
+    T* vec = (l == L) ? x : lvec(l);
     const int ldv = (l == L) ? ld : P.n * P.b;
     // Qᵀ then the forward triangular sweep: fused in one launch where the level
     // is narrow (the launches, not the flops, set its time), else three
     // batched GEMMs and the sweep
     const bool fused = P.n <= kFuseNodes;
-    if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/true, st);
+    if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/true, st, col0);
     Launch k(h, HSS_K_TRSV_FWD,
              (trsv_flops(P.b, P.c, nc) + (fused ? qapply_flops(P.b, r, nc) : 0.0)) * P.n, st,
              sizeof(T) == 4);
-    HSS_TRY(launch_ulv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                              Q.n * Q.b, r, fused ? P.V : nullptr, (long long)P.b * r, P.T_,
-                              (long long)r * r, r, P.n, st, h->staging));
+    HSS_TRY(launch_ulv_fwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc,
+                              lvec(l - 1), Q.n * Q.b, r, fused ? P.V : nullptr,
+                              (long long)P.b * r, P.T_, (long long)r * r, r, P.n, st,
+                              h->staging));
   }
   if (lo >= 1) {
     Launch k(h, HSS_K_TRSV_FWD, tree_flops, st, sizeof(T) == 4);
-    HSS_TRY(launch_tree_fwd<T>(tl, lo, 2 * r, r, r, nc, h->tree_cnt, st));
+    HSS_TRY(launch_tree_fwd<T>(tl, lo, 2 * r, r, r, nc, ln.tcnt, st));
   }
   const int b0 = 2 * r;
+  const long long rc0 = (long long)col0 * b0;
   double* rootA;
   double* rv;
   if (sizeof(T) == sizeof(double)) {
     rootA = reinterpret_cast<double*>(f.lv[0].A);
-    rv = reinterpret_cast<double*>(f.lv[0].yv);
+    rv = reinterpret_cast<double*>(lvec(0));
   } else {
     rootA = h->R0;
-    rv = h->root_vec;
+    rv = h->root_vec + rc0;
     Launch k(h, HSS_K_OTHER, 0.0, st);
-    launch_f32_to_f64(reinterpret_cast<const float*>(f.lv[0].yv), rv, (long long)b0 * nc, st);
+    launch_f32_to_f64(reinterpret_cast<const float*>(lvec(0)), rv, (long long)b0 * nc, st);
   }
   if (sizeof(T) != sizeof(double) && h->a0inv_valid) {
-    gemm<double>(h, false, false, b0, nc, b0, 1.0, h->A0inv, b0, 0, rv, b0, 0, 0.0, h->root_vec2,
-                 b0, 0, 1, st);
-    rv = h->root_vec2;
+    gemm<double>(h, false, false, b0, nc, b0, 1.0, h->A0inv, b0, 0, rv, b0, 0, 0.0,
+                 h->root_vec2 + rc0, b0, 0, 1, st);
+    rv = h->root_vec2 + rc0;
   } else {
     {
       Launch k(h, HSS_K_TRSV_FWD, trsv_flops(b0, b0, nc), st);
@@ -687,19 +714,18 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
   }
   if (sizeof(T) != sizeof(double)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
-    launch_f64_to_f32(rv, reinterpret_cast<float*>(f.lv[0].yv), (long long)b0 * nc, st);
+    launch_f64_to_f32(rv, reinterpret_cast<float*>(lvec(0)), (long long)b0 * nc, st);
   }
   if (lo >= 1) {
     const long long wl = h->wait_budget > 0 ? h->wait_budget : (h->wait_budget < 0 ? 0 : 1LL << 24);
-    if (++h->tree_epoch <= 0) h->tree_epoch = 1;
+    if (++ln.epoch <= 0) ln.epoch = 1;
     Launch k(h, HSS_K_TRSV_BWD, tree_flops, st, sizeof(T) == 4);
-    HSS_TRY(launch_tree_bwd<T>(tl, lo, 2 * r, r, r, nc, h->tree_ready, h->tree_epoch, wl,
-                               h->status, st));
+    HSS_TRY(launch_tree_bwd<T>(tl, lo, 2 * r, r, r, nc, ln.tready, ln.epoch, wl, h->status, st));
   }
   for (int l = lo + 1; l <= L; ++l) {
     LevelT<T>& P = f.lv[l];
     LevelT<T>& Q = f.lv[l - 1];
-    T* vec = (l == L) ? x : P.yv;
+    T* vec = (l == L) ? x : lvec(l);
     const int ldv = (l == L) ? ld : P.n * P.b;
     // the backward triangular sweep then Q (fused where the level is narrow)
     const bool fused = P.n <= kFuseNodes;
@@ -707,55 +733,62 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st) 
       Launch k(h, HSS_K_TRSV_BWD,
                (trsv_flops(P.b, P.c, nc) + (fused ? qapply_flops(P.b, r, nc) : 0.0)) * P.n, st,
                sizeof(T) == 4);
-      HSS_TRY(launch_ulv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc, Q.yv,
-                                Q.n * Q.b, r, fused ? P.V : nullptr, (long long)P.b * r, P.T_,
-                                (long long)r * r, r, P.n, st, h->staging));
+      HSS_TRY(launch_ulv_bwd<T>(P.M, P.b, (long long)P.b * P.b, P.b, P.c, vec, ldv, P.b, nc,
+                                lvec(l - 1), Q.n * Q.b, r, fused ? P.V : nullptr,
+                                (long long)P.b * r, P.T_, (long long)r * r, r, P.n, st,
+                                h->staging));
     }
-    if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/false, st);
+    if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/false, st, col0);
   }
   return check_launch();
 }
 
+// y = A x in FP64 on lane g's streams, using columns col0 .. of the per-level
+// scratch (nrhs <= kMaxCols - col0 when col0 > 0)
 int matvec_fp64(hss_s* h, const double* x, int ldx, double* y, int ldy, int nrhs,
-                cudaStream_t st) {
+                cudaStream_t st, int g = 0, int col0 = 0) {
   const int L = h->L, r = h->rank, leaf = h->leaf;
   const long long rr = (long long)r * r;
   const int nL = 1 << L;
-  const cudaStream_t ms = h->serialize ? st : h->mstream;
-  for (int j0 = 0; j0 < nrhs; j0 += kMaxCols) {
-    const int nc = std::min(kMaxCols, nrhs - j0);
+  Lane& ln = h->lane[g];
+  const cudaStream_t ms = h->serialize ? st : ln.ms;
+  // this lane's columns of the level vectors x̂_l, ŷ_l ((2^l r) x kMaxCols each)
+  auto xh = [&](int l) { return h->xh[l] + (long long)col0 * ((1LL << l) * r); };
+  auto yh = [&](int l) { return h->yh[l] + (long long)col0 * ((1LL << l) * r); };
+  for (int j0 = 0, nc = 0; j0 < nrhs; j0 += nc) {
+    nc = std::min(kMaxCols - col0, nrhs - j0);   // passes of at most kMaxCols - col0 columns
     const double* xc = x + (long long)j0 * ldx;
     double* yc = y + (long long)j0 * ldy;
     // leaves, first part: y = D x, which needs nothing else, on the second
     // stream while the basis sweeps below run on the caller's
-    if (cudaEventRecord(h->ev_mv_start, st) != cudaSuccess ||
-        cudaStreamWaitEvent(ms, h->ev_mv_start, 0) != cudaSuccess)
+    if (cudaEventRecord(ln.mv_start, st) != cudaSuccess ||
+        cudaStreamWaitEvent(ms, ln.mv_start, 0) != cudaSuccess)
       return HSS_ERR_CUDA;
     gemm<double>(h, false, false, leaf, nc, leaf, 1.0, h->D, leaf, (long long)leaf * leaf, xc, ldx,
                  leaf, 0.0, yc, ldy, leaf, nL, ms);
-    if (cudaEventRecord(h->ev_mv_dx, ms) != cudaSuccess) return HSS_ERR_CUDA;
+    if (cudaEventRecord(ln.mv_dx, ms) != cudaSuccess) return HSS_ERR_CUDA;
     // up-sweep: x̂_L = Uᵀ x, x̂_l = E_lᵀ [x̂_{l+1}(2p); x̂_{l+1}(2p+1)]
     gemm<double>(h, true, false, r, nc, leaf, 1.0, h->U, leaf, (long long)leaf * r, xc, ldx, leaf,
-                 0.0, h->xh[L], nL * r, r, nL, st);
+                 0.0, xh(L), nL * r, r, nL, st);
     for (int l = L - 1; l >= 1; --l)
-      gemm<double>(h, true, false, r, nc, 2 * r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, h->xh[l + 1],
-                   (2 << l) * r, 2 * r, 0.0, h->xh[l], (1 << l) * r, r, 1 << l, st);
+      gemm<double>(h, true, false, r, nc, 2 * r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, xh(l + 1),
+                   (2 << l) * r, 2 * r, 0.0, xh(l), (1 << l) * r, r, 1 << l, st);
     // sibling couplings of every level (these initialise ŷ)
     for (int l = 1; l <= L; ++l) {
       const double* Sl = h->S + h->Soff[l];
       const int ldl = (1 << l) * r;
-      gemm<double>(h, false, false, r, nc, r, 1.0, Sl, r, rr, h->xh[l], ldl, 2 * r, 0.0,
-                   h->yh[l] + r, ldl, 2 * r, 1 << (l - 1), st);
-      gemm<double>(h, true, false, r, nc, r, 1.0, Sl, r, rr, h->xh[l] + r, ldl, 2 * r, 0.0,
-                   h->yh[l], ldl, 2 * r, 1 << (l - 1), st);
+      gemm<double>(h, false, false, r, nc, r, 1.0, Sl, r, rr, xh(l), ldl, 2 * r, 0.0, yh(l) + r,
+                   ldl, 2 * r, 1 << (l - 1), st);
+      gemm<double>(h, true, false, r, nc, r, 1.0, Sl, r, rr, xh(l) + r, ldl, 2 * r, 0.0, yh(l),
+                   ldl, 2 * r, 1 << (l - 1), st);
     }
     // down-sweep: ŷ_{l+1}(children) += E_l ŷ_l
     for (int l = 1; l <= L - 1; ++l)
-      gemm<double>(h, false, false, 2 * r, nc, r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, h->yh[l],
-                   (1 << l) * r, r, 1.0, h->yh[l + 1], (2 << l) * r, 2 * r, 1 << l, st);
+      gemm<double>(h, false, false, 2 * r, nc, r, 1.0, h->E + h->Eoff[l], 2 * r, 2 * rr, yh(l),
+                   (1 << l) * r, r, 1.0, yh(l + 1), (2 << l) * r, 2 * r, 1 << l, st);
     // leaves, second part: y += U ŷ once D x is done
-    if (cudaStreamWaitEvent(st, h->ev_mv_dx, 0) != cudaSuccess) return HSS_ERR_CUDA;
-    gemm<double>(h, false, false, leaf, nc, r, 1.0, h->U, leaf, (long long)leaf * r, h->yh[L],
+    if (cudaStreamWaitEvent(st, ln.mv_dx, 0) != cudaSuccess) return HSS_ERR_CUDA;
+    gemm<double>(h, false, false, leaf, nc, r, 1.0, h->U, leaf, (long long)leaf * r, yh(L),
                  nL * r, r, 1.0, yc, ldy, leaf, nL, st);
     int rc = check_launch();
     if (rc) return rc;
@@ -882,9 +915,21 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
   double* ib = h->norms + kSolveCols;       // 1 / |b|
   double* nr = h->norms + 2 * kSolveCols;   // |r|
   double* ir = h->norms + 3 * kSolveCols;   // 1 / |r|
+  // pinned host copies: |b|, |r| per column, then each lane's status word
+  double* hnb = h->hnorm;
+  double* hnr = h->hnorm + kSolveCols;
+  int* hst = reinterpret_cast<int*>(h->hnorm + 2 * kSolveCols);
   int worst_it = 0;
   double worst_res = 0.0;
   int result = HSS_OK;
+  // one refinement lane: columns c0 .. c0+nc-1 of the pass on stream ls
+  struct IrLane {
+    int g, c0, nc;
+    cudaStream_t ls;
+    int it = 0;
+    double rel = 0.0;
+    bool active = false;
+  };
   for (int j0 = 0; j0 < nrhs; j0 += kSolveCols) {
     const int nc = std::min(kSolveCols, nrhs - j0);
     const double* bc = b + (long long)j0 * ld;
@@ -897,61 +942,115 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
       bc = h->bbuf;
       ldb = n;
     }
-    {
-      Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
-      launch_col_norms(bc, ldb, n, nc, nb, ib, h->norm_part, st);
-    }
-    {
-      Launch k(h, HSS_K_OTHER, 0.0, st);
-      launch_cols_to_f32(bc, ldb, f.d, n, n, nc, ib, st);
-    }
-    int rc = solve_sweeps<float>(h, f, f.d, nc, n, st);
-    if (rc) return rc;
-    {
-      Launch k(h, HSS_K_OTHER, 0.0, st);
-      launch_cols_update(xc, ld, f.d, n, n, nc, nb, /*accumulate=*/0, st);
-    }
-    double hnb[kSolveCols], hnr[kSolveCols];
-    if (cudaMemcpyAsync(hnb, nb, sizeof(double) * nc, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-      return HSS_ERR_CUDA;
-    int it = 0;
-    double rel = 0.0;
-    for (;; ++it) {
-      rc = h->residual == HSS_RESIDUAL_PAIR32
-               ? matvec_pair(h, xc, ld, h->rbuf, n, nc, st)    // rbuf: n x nc, ld = n
-               : matvec_fp64(h, xc, ld, h->rbuf, n, nc, st);
-      if (rc) return rc;
-      {
-        Launch k(h, HSS_K_OTHER, (double)n * nc, st);
-        launch_residual(bc, ldb, h->rbuf, n, n, nc, st);
-      }
-      {
-        Launch k(h, HSS_K_OTHER, 2.0 * n * nc, st);
-        launch_col_norms(h->rbuf, n, n, nc, nr, ir, h->norm_part, st);
-      }
-      if (cudaMemcpyAsync(hnr, nr, sizeof(double) * nc, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    // two lanes over the columns when there are two columns or more (the pair
+    // residual's split buffers are shared, and a serialized trace times one
+    // stream: one lane)
+    const int lanes = (nc >= 2 && h->ir_lanes == 2 && h->residual == HSS_RESIDUAL_FP64 &&
+                       !h->serialize) ? 2 : 1;
+    IrLane lane[2];
+    lane[0].g = 0;
+    lane[0].c0 = 0;
+    lane[0].nc = lanes == 2 ? (nc + 1) / 2 : nc;
+    lane[0].ls = st;
+    lane[1].g = 1;
+    lane[1].c0 = lane[0].nc;
+    lane[1].nc = nc - lane[0].nc;
+    lane[1].ls = h->lane[1].st;
+    if (lanes == 2) {
+      if (cudaEventRecord(h->ev_ir_fork, st) != cudaSuccess ||
+          cudaStreamWaitEvent(lane[1].ls, h->ev_ir_fork, 0) != cudaSuccess)
         return HSS_ERR_CUDA;
-      if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
-      int s[8];
-      int code = read_status(h, s);
-      if (code) return code;
-      rel = 0.0;
-      for (int j = 0; j < nc; ++j) rel = std::max(rel, hnb[j] > 0 ? hnr[j] / hnb[j] : hnr[j]);
-      if (!(rel > h->ir_tol) || it >= h->ir_max_it) break;
-      {
-        Launch k(h, HSS_K_OTHER, 0.0, st);
-        launch_cols_to_f32(h->rbuf, n, f.d, n, n, nc, ir, st);
-      }
-      rc = solve_sweeps<float>(h, f, f.d, nc, n, st);
+    }
+    // residual r = b - A x of a lane, its norms and the status word to the host
+    auto residual_step = [&](IrLane& q) -> int {
+      const long long o = (long long)q.c0 * n;
+      int rc = h->residual == HSS_RESIDUAL_PAIR32
+                   ? matvec_pair(h, xc, ld, h->rbuf, n, q.nc, q.ls)
+                   : matvec_fp64(h, xc + (long long)q.c0 * ld, ld, h->rbuf + o, n, q.nc, q.ls,
+                                 q.g, q.c0);
       if (rc) return rc;
       {
-        Launch k(h, HSS_K_OTHER, (double)n * nc, st);
-        launch_cols_update(xc, ld, f.d, n, n, nc, nr, /*accumulate=*/1, st);
+        Launch k(h, HSS_K_OTHER, (double)n * q.nc, q.ls);
+        launch_residual(bc + (long long)q.c0 * ldb, ldb, h->rbuf + o, n, n, q.nc, q.ls);
+      }
+      {
+        Launch k(h, HSS_K_OTHER, 2.0 * n * q.nc, q.ls);
+        launch_col_norms(h->rbuf + o, n, n, q.nc, nr + q.c0, ir + q.c0,
+                         h->norm_part + 64LL * q.c0, q.ls);
+      }
+      if (cudaMemcpyAsync(hnr + q.c0, nr + q.c0, sizeof(double) * q.nc, cudaMemcpyDeviceToHost,
+                          q.ls) != cudaSuccess ||
+          cudaMemcpyAsync(hst + 8 * q.g, h->status, 8 * sizeof(int), cudaMemcpyDeviceToHost,
+                          q.ls) != cudaSuccess ||
+          cudaEventRecord(h->lane[q.g].norm_ready, q.ls) != cudaSuccess)
+        return HSS_ERR_CUDA;
+      return HSS_OK;
+    };
+    // d = M⁻¹ v in FP32 (v scaled by scale), x = x (+)= d unscaled
+    auto correction = [&](IrLane& q, const double* v, int ldv, const double* scale,
+                          const double* unscale, int accumulate) -> int {
+      const long long o = (long long)q.c0 * n;
+      {
+        Launch k(h, HSS_K_OTHER, 0.0, q.ls);
+        launch_cols_to_f32(v, ldv, f.d + o, n, n, q.nc, scale, q.ls);
+      }
+      int rc = solve_sweeps<float>(h, f, f.d + o, q.nc, n, q.ls, q.g, q.c0);
+      if (rc) return rc;
+      Launch k(h, HSS_K_OTHER, accumulate ? (double)n * q.nc : 0.0, q.ls);
+      launch_cols_update(xc + (long long)q.c0 * ld, ld, f.d + o, n, n, q.nc, unscale, accumulate,
+                         q.ls);
+      return HSS_OK;
+    };
+    for (int g = 0; g < lanes; ++g) {   // x_0 = M⁻¹ b, then the first residual
+      IrLane& q = lane[g];
+      {
+        Launch k(h, HSS_K_OTHER, 2.0 * n * q.nc, q.ls);
+        launch_col_norms(bc + (long long)q.c0 * ldb, ldb, n, q.nc, nb + q.c0, ib + q.c0,
+                         h->norm_part + 64LL * q.c0, q.ls);
+      }
+      if (cudaMemcpyAsync(hnb + q.c0, nb + q.c0, sizeof(double) * q.nc, cudaMemcpyDeviceToHost,
+                          q.ls) != cudaSuccess)
+        return HSS_ERR_CUDA;
+      int rc = correction(q, bc + (long long)q.c0 * ldb, ldb, ib + q.c0, nb + q.c0, 0);
+      if (rc) return rc;
+      rc = residual_step(q);
+      if (rc) return rc;
+      q.active = true;
+    }
+    // each lane: wait for its own residual norms only, then queue its next
+    // correction and residual; the other lane's work stays in flight
+    for (bool any = true; any;) {
+      any = false;
+      for (int g = 0; g < lanes; ++g) {
+        IrLane& q = lane[g];
+        if (!q.active) continue;
+        if (cudaEventSynchronize(h->lane[g].norm_ready) != cudaSuccess) return HSS_ERR_CUDA;
+        if (hst[8 * g + ST_CODE]) return hst[8 * g + ST_CODE];
+        q.rel = 0.0;
+        for (int j = q.c0; j < q.c0 + q.nc; ++j)
+          q.rel = std::max(q.rel, hnb[j] > 0 ? hnr[j] / hnb[j] : hnr[j]);
+        if (!(q.rel > h->ir_tol) || q.it >= h->ir_max_it) {
+          q.active = false;
+          continue;
+        }
+        ++q.it;
+        int rc = correction(q, h->rbuf + (long long)q.c0 * n, n, ir + q.c0, nr + q.c0, 1);
+        if (rc) return rc;
+        rc = residual_step(q);
+        if (rc) return rc;
+        any = true;
       }
     }
-    worst_it = std::max(worst_it, it);
-    worst_res = std::max(worst_res, rel);
-    if (rel > h->ir_tol || !(rel == rel)) result = HSS_ERR_NO_CONVERGENCE;
+    if (lanes == 2) {
+      if (cudaEventRecord(h->ev_ir_join, lane[1].ls) != cudaSuccess ||
+          cudaStreamWaitEvent(st, h->ev_ir_join, 0) != cudaSuccess)
+        return HSS_ERR_CUDA;
+    }
+    for (int g = 0; g < lanes; ++g) {
+      worst_it = std::max(worst_it, lane[g].it);
+      worst_res = std::max(worst_res, lane[g].rel);
+      if (lane[g].rel > h->ir_tol || !(lane[g].rel == lane[g].rel)) result = HSS_ERR_NO_CONVERGENCE;
+    }
   }
   h->ir_iters = worst_it;
   h->ir_resid = worst_res;
@@ -1025,7 +1124,8 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   if (L >= 2) e = e ? e : cudaMemcpy(h->E, E, sizeof(double) * h->esz, kind);
   e = e ? e : cudaMemcpy(h->S, S, sizeof(double) * h->ssz, kind);
   e = e ? e : cudaMemset(h->status, 0, 8 * sizeof(int));
-  e = e ? e : cudaMemset(h->tree_ready, 0, sizeof(int) << (kTreeTop + 1));
+  for (Lane& ln : h->lane)
+    e = e ? e : cudaMemset(ln.tready, 0, sizeof(int) << (kTreeTop + 1));
   if (h->uneven)
     e = e ? e : cudaMemcpy(h->pmap, pad.pmap.data(), sizeof(int) * h->n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -1035,10 +1135,19 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   }
   h->ev_level.assign(L + 1, nullptr);
   e = cudaStreamCreateWithFlags(&h->qstream, cudaStreamNonBlocking);
-  e = e ? e : cudaStreamCreateWithFlags(&h->mstream, cudaStreamNonBlocking);
   e = e ? e : cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
-  e = e ? e : cudaEventCreateWithFlags(&h->ev_mv_start, cudaEventDisableTiming);
-  e = e ? e : cudaEventCreateWithFlags(&h->ev_mv_dx, cudaEventDisableTiming);
+  e = e ? e : cudaEventCreateWithFlags(&h->ev_ir_fork, cudaEventDisableTiming);
+  e = e ? e : cudaEventCreateWithFlags(&h->ev_ir_join, cudaEventDisableTiming);
+  for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+    Lane& ln = h->lane[g];
+    if (g == 1) e = cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking);
+    e = e ? e : cudaStreamCreateWithFlags(&ln.ms, cudaStreamNonBlocking);
+    e = e ? e : cudaEventCreateWithFlags(&ln.mv_start, cudaEventDisableTiming);
+    e = e ? e : cudaEventCreateWithFlags(&ln.mv_dx, cudaEventDisableTiming);
+    e = e ? e : cudaEventCreateWithFlags(&ln.norm_ready, cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess && cudaMallocHost(&h->hnorm, sizeof(double) * 2 * kSolveCols + 16 * sizeof(int)) != cudaSuccess)
+    e = cudaErrorMemoryAllocation;
   for (int l = 1; l <= L && e == cudaSuccess; ++l)
     e = cudaEventCreateWithFlags(&h->ev_level[l], cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -1059,11 +1168,18 @@ void hss_destroy(hss_t h) {
   for (cudaEvent_t ev : h->ev_level)
     if (ev) cudaEventDestroy(ev);
   if (h->ev_start) cudaEventDestroy(h->ev_start);
-  if (h->ev_mv_start) cudaEventDestroy(h->ev_mv_start);
-  if (h->ev_mv_dx) cudaEventDestroy(h->ev_mv_dx);
-  if (h->mstream) cudaStreamSynchronize(h->mstream);
+  if (h->ev_ir_fork) cudaEventDestroy(h->ev_ir_fork);
+  if (h->ev_ir_join) cudaEventDestroy(h->ev_ir_join);
+  for (Lane& ln : h->lane) {
+    for (cudaStream_t s : {ln.st, ln.ms})
+      if (s) cudaStreamSynchronize(s);
+    for (cudaEvent_t ev : {ln.mv_start, ln.mv_dx, ln.norm_ready})
+      if (ev) cudaEventDestroy(ev);
+    if (ln.st) cudaStreamDestroy(ln.st);
+    if (ln.ms) cudaStreamDestroy(ln.ms);
+  }
+  if (h->hnorm) cudaFreeHost(h->hnorm);
   if (h->qstream) cudaStreamDestroy(h->qstream);
-  if (h->mstream) cudaStreamDestroy(h->mstream);
   cudaFree(h->arena);
   if (h->f32.arena) cudaFree(h->f32.arena);
   if (h->tc_ws) cudaFree(h->tc_ws);
