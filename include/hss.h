@@ -147,7 +147,11 @@ typedef struct {
                           already issued always uses the default, so that tensor memory
                           is never released under a pending MMA. */
   int32_t schedule;    /* hss_schedule: how the solve's upper levels are launched */
-  int32_t reserved;    /* 0 */
+  int32_t ql_panel;    /* columns per register panel of the Householder basis kernel:
+                          16 or 32 in the FP32 arithmetic (FP64 always 16); 0 = the
+                          default (32 in FP32).  With basis = HSS_BASIS_AUTO the
+                          choice of hss_tune is used instead.  Other values:
+                          HSS_ERR_INVALID_ARG. */
 } hss_options;
 
 /* Create a device-resident HSS object from its generators (format above).
@@ -239,10 +243,12 @@ int hss_matvec_noalloc(const hss_shape* shape, const double* D, const double* U,
                        void* stream);
 
 /* Choices of the autotuner (hss_tune) for one object: the basis method, the
- * schedule of the solve's upper levels, the panel staging of the solve's sweep
- * kernels (0 = the largest shared-memory panels, 1 = the panels that let the
- * fewest waves of CTAs cover a level), and the measured times of the chosen
- * configuration. */
+ * panel width of the Householder basis kernel (16 or 32 columns: the wider
+ * panel holds more of the basis in registers, the narrower one lets two CTAs
+ * share an SM), the schedule of the solve's upper levels, the panel staging of
+ * the solve's sweep kernels (0 = the largest shared-memory panels, 1 = the
+ * panels that let the fewest waves of CTAs cover a level), and the measured
+ * times of the chosen configuration. */
 typedef struct {
   int32_t basis;      /* hss_basis_method */
   int32_t schedule;   /* hss_schedule */
@@ -252,11 +258,16 @@ typedef struct {
   double solve_ms;    /* one solve of min(nrhs, 16) columns with the chosen schedule */
   double factor_ms_by_basis[2];        /* every candidate measured: [basis method] */
   double solve_ms_by_config[2][2];     /* [schedule][staging]; 0 where not measured */
+  int32_t ql_panel;                    /* 16 or 32 */
+  int32_t reserved;
+  double factor_ms_by_panel[2];        /* Householder basis with 16 / 32-column panels;
+                                          0 where not measured (FP64 has 16 only) */
 } hss_tuning;
 
 /* Autotuner: for the object's shape and the arithmetic of opt (precision,
  * residual), times every candidate configuration on the object itself with
- * CUDA events on `stream` -- each basis method on hss_factorize, each pair of
+ * CUDA events on `stream` -- each basis method (the Householder one with each
+ * panel width its arithmetic has) on hss_factorize, each pair of
  * solve schedule and sweep panel staging on hss_solve of min(nrhs, 16)
  * columns of a fixed test vector -- best of two runs each, and keeps the
  * fastest; later hss_factorize calls with basis = HSS_BASIS_AUTO or schedule =

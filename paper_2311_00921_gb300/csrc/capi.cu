@@ -117,6 +117,8 @@ struct hss_s {
   int staging = 0;                     // panel staging of the sweep kernels (see launch_ulv_fwd)
   int tuned = 0;                       // hss_tune has chosen the following
   int tuned_basis = HSS_BASIS_HOUSEHOLDER, tuned_schedule = HSS_SCHEDULE_ASYNC, tuned_staging = 0;
+  int tuned_panel = 0;
+  int ql_panel = 0;                    // register panel of the Householder basis kernel (0 = default)
 
   // pair-of-FP32 generators (hi parts are the FP32 factor's converted copies)
   // and the pair matvec's vectors, in the FP32 arena
@@ -437,7 +439,8 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
     } else {
       Launch k(h, HSS_K_QL, (2.0 * b * r * r - 2.0 / 3.0 * r * r * r + 1.0 * b * r * r) * n, qs,
                sizeof(T) == 4);
-      HSS_TRY(launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, qs));
+      HSS_TRY(launch_ql_basis<T>(Bsrc, b, br, P.V, br, P.T_, rr, P.LB, rr, b, r, n, qs, nullptr,
+                                 h->ql_panel));
     }
     // (d, first half) merge: Ŝ = L_B(c2) S L_B(c1)ᵀ and Ŝᵀ into the parent's
     // off-diagonal blocks, parent basis blkdiag(L_B(c1), L_B(c2)) E_p
@@ -653,7 +656,10 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st, 
   // level l's vector, this lane's columns
   auto lvec = [&](int l) { return f.lv[l].yv + (long long)col0 * f.lv[l].n * f.lv[l].b; };
   // levels lo .. 1 (the narrow top of the tree) run as one launch per direction
-  const int lo = h->schedule == HSS_SCHEDULE_ASYNC ? std::min(L - 1, kTreeTop) : 0;
+  // where the tree kernels' shared memory fits
+  const int lo = (h->schedule == HSS_SCHEDULE_ASYNC && tree_fits<T>(2 * r, nc, r))
+                     ? std::min(L - 1, kTreeTop)
+                     : 0;
   TreeLevels<T> tl{};
   double tree_flops = 0.0;
   for (int l = 0; l <= lo; ++l) {
@@ -669,9 +675,9 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st, 
     T* vec = (l == L) ? x : lvec(l);
     const int ldv = (l == L) ? ld : P.n * P.b;
     // Qᵀ then the forward triangular sweep: fused in one launch where the level
-    // is narrow (the launches, not the flops, set its time), else three
-    // batched GEMMs and the sweep
-    const bool fused = P.n <= kFuseNodes;
+    // is narrow (the launches, not the flops, set its time) and the fused
+    // kernel's shared memory fits, else three batched GEMMs and the sweep
+    const bool fused = P.n <= kFuseNodes && ulv_fused_fits<T>(P.b, nc, r, false);
     if (!fused) apply_q<T>(h, f, P, vec, ldv, nc, /*transpose=*/true, st, col0);
     Launch k(h, HSS_K_TRSV_FWD,
              (trsv_flops(P.b, P.c, nc) + (fused ? qapply_flops(P.b, r, nc) : 0.0)) * P.n, st,
@@ -727,8 +733,9 @@ int solve_sweeps(hss_s* h, Factor<T>& f, T* x, int nc, int ld, cudaStream_t st, 
     LevelT<T>& Q = f.lv[l - 1];
     T* vec = (l == L) ? x : lvec(l);
     const int ldv = (l == L) ? ld : P.n * P.b;
-    // the backward triangular sweep then Q (fused where the level is narrow)
-    const bool fused = P.n <= kFuseNodes;
+    // the backward triangular sweep then Q (fused where the level is narrow and
+    // the fused kernel fits)
+    const bool fused = P.n <= kFuseNodes && ulv_fused_fits<T>(P.b, nc, r, true);
     {
       Launch k(h, HSS_K_TRSV_BWD,
                (trsv_flops(P.b, P.c, nc) + (fused ? qapply_flops(P.b, r, nc) : 0.0)) * P.n, st,
@@ -956,11 +963,6 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
     lane[1].c0 = lane[0].nc;
     lane[1].nc = nc - lane[0].nc;
     lane[1].ls = h->lane[1].st;
-    if (lanes == 2) {
-      if (cudaEventRecord(h->ev_ir_fork, st) != cudaSuccess ||
-          cudaStreamWaitEvent(lane[1].ls, h->ev_ir_fork, 0) != cudaSuccess)
-        return HSS_ERR_CUDA;
-    }
     // residual r = b - A x of a lane, its norms and the status word to the host
     auto residual_step = [&](IrLane& q) -> int {
       const long long o = (long long)q.c0 * n;
@@ -1013,6 +1015,12 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
         return HSS_ERR_CUDA;
       int rc = correction(q, bc + (long long)q.c0 * ldb, ldb, ib + q.c0, nb + q.c0, 0);
       if (rc) return rc;
+      // lane 1 starts once lane 0's first sweeps are done: from then on one
+      // lane's FP32 sweeps run beside the other lane's FP64 matvec
+      if (g == 0 && lanes == 2 &&
+          (cudaEventRecord(h->ev_ir_fork, q.ls) != cudaSuccess ||
+           cudaStreamWaitEvent(lane[1].ls, h->ev_ir_fork, 0) != cudaSuccess))
+        return HSS_ERR_CUDA;
       rc = residual_step(q);
       if (rc) return rc;
       q.active = true;
@@ -1200,6 +1208,8 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     return HSS_ERR_INVALID_ARG;
   if (opt && (opt->schedule < HSS_SCHEDULE_ASYNC || opt->schedule > HSS_SCHEDULE_AUTO))
     return HSS_ERR_INVALID_ARG;
+  if (opt && opt->ql_panel != 0 && opt->ql_panel != 16 && opt->ql_panel != 32)
+    return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
   if (prec != HSS_FP64) {
@@ -1214,12 +1224,14 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     h->basis_method = opt->basis == HSS_BASIS_AUTO
                           ? (h->tuned ? h->tuned_basis : HSS_BASIS_HOUSEHOLDER)
                           : opt->basis;
+    h->ql_panel = opt->basis == HSS_BASIS_AUTO && h->tuned ? h->tuned_panel : opt->ql_panel;
     const bool sauto = opt->schedule == HSS_SCHEDULE_AUTO;
     h->schedule = sauto ? (h->tuned ? h->tuned_schedule : HSS_SCHEDULE_ASYNC) : opt->schedule;
     h->staging = sauto && h->tuned ? h->tuned_staging : 0;
   } else {
     h->wait_budget = 0;
     h->basis_method = HSS_BASIS_HOUSEHOLDER;
+    h->ql_panel = 0;
     h->schedule = HSS_SCHEDULE_ASYNC;
     h->staging = 0;
   }
@@ -1369,9 +1381,11 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
       while (fgets(line, sizeof line, f)) {
         if (strncmp(line, key, kl) != 0 || line[kl] != ' ') continue;
         hss_tuning t{};
-        if (sscanf(line + kl, " basis %d schedule %d staging %d factor_ms %lf solve_ms %lf",
-                   &t.basis, &t.schedule, &t.staging, &t.factor_ms, &t.solve_ms) == 5 &&
+        if (sscanf(line + kl, " basis %d panel %d schedule %d staging %d factor_ms %lf solve_ms %lf",
+                   &t.basis, &t.ql_panel, &t.schedule, &t.staging, &t.factor_ms,
+                   &t.solve_ms) == 6 &&
             t.basis >= HSS_BASIS_HOUSEHOLDER && t.basis <= HSS_BASIS_CHOLQR &&
+            (t.ql_panel == 16 || t.ql_panel == 32) &&
             t.schedule >= HSS_SCHEDULE_ASYNC && t.schedule <= HSS_SCHEDULE_LEVELS &&
             (t.staging == 0 || t.staging == 1)) {
           best = t;
@@ -1416,21 +1430,41 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
     best.factor_ms = 1e30;
     const bool cholqr_ok = o.precision == HSS_FP64 ? h->rank <= basis_max_rank<double>()
                                                   : h->rank <= basis_max_rank<float>();
-    for (int basis = HSS_BASIS_HOUSEHOLDER; rc == HSS_OK && basis <= HSS_BASIS_CHOLQR; ++basis) {
-      if (basis == HSS_BASIS_CHOLQR && !cholqr_ok) continue;
-      o.basis = basis;
+    // candidates: the Householder kernel with each panel width (FP32 has 16
+    // and 32 columns, FP64 16), then Cholesky QR; through the tuned path of
+    // hss_factorize so that each runs exactly as it will be used
+    struct Cand { int basis, panel; };
+    const Cand cands[3] = {{HSS_BASIS_HOUSEHOLDER, 32}, {HSS_BASIS_HOUSEHOLDER, 16},
+                           {HSS_BASIS_CHOLQR, 16}};
+    for (const Cand& cd : cands) {
+      if (rc != HSS_OK) break;
+      if (cd.basis == HSS_BASIS_CHOLQR && !cholqr_ok) continue;
+      if (cd.panel == 32 && o.precision == HSS_FP64) continue;
+      h->tuned = 1;
+      h->tuned_basis = cd.basis;
+      h->tuned_panel = cd.panel;
+      o.basis = HSS_BASIS_AUTO;
       o.schedule = HSS_SCHEDULE_ASYNC;
       double ms = 0.0;
       rc = timed([&] { return hss_factorize(h, &o, st); }, &ms);
-      if (rc == HSS_OK) best.factor_ms_by_basis[basis] = ms;
-      if (rc == HSS_OK && ms < best.factor_ms) {
+      if (rc != HSS_OK) break;
+      double& by_basis = best.factor_ms_by_basis[cd.basis];
+      by_basis = by_basis > 0 ? std::min(by_basis, ms) : ms;
+      if (cd.basis == HSS_BASIS_HOUSEHOLDER) best.factor_ms_by_panel[cd.panel == 32] = ms;
+      if (ms < best.factor_ms) {
         best.factor_ms = ms;
-        best.basis = basis;
+        best.basis = cd.basis;
+        best.ql_panel = cd.panel;
       }
     }
-    if (rc == HSS_OK) {
-      o.basis = best.basis;
+    h->tuned = 0;
+    if (rc == HSS_OK) {   // leave the object factorized with the choice
+      h->tuned_panel = best.ql_panel;
+      h->tuned = 1;
+      h->tuned_basis = best.basis;
+      o.basis = HSS_BASIS_AUTO;
       rc = hss_factorize(h, &o, st);
+      h->tuned = 0;
     }
     best.solve_ms = 1e30;
     for (int sched = HSS_SCHEDULE_ASYNC; rc == HSS_OK && sched <= HSS_SCHEDULE_LEVELS; ++sched) {
@@ -1454,14 +1488,16 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
     if (rc) return rc;
     if (cache_path) {
       if (FILE* f = fopen(cache_path, "a")) {
-        fprintf(f, "%s basis %d schedule %d staging %d factor_ms %.4f solve_ms %.4f\n", key,
-                best.basis, best.schedule, best.staging, best.factor_ms, best.solve_ms);
+        fprintf(f, "%s basis %d panel %d schedule %d staging %d factor_ms %.4f solve_ms %.4f\n",
+                key, best.basis, best.ql_panel, best.schedule, best.staging, best.factor_ms,
+                best.solve_ms);
         fclose(f);
       }
     }
   }
   h->tuned = 1;
   h->tuned_basis = best.basis;
+  h->tuned_panel = best.ql_panel;
   h->tuned_schedule = best.schedule;
   h->tuned_staging = best.staging;
   o.basis = HSS_BASIS_AUTO;

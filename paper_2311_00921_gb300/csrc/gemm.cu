@@ -157,29 +157,32 @@ gemm_skinny_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int ld
   }
 }
 
-// n <= 16 columns: CTA = 128 rows x 16 columns, 128 threads with a 4 x 4
-// register micro-tile each (rows lane + 32 p, columns warp + 4 q): 16 FMAs per
-// 8 shared-memory loads, as in the square tile, so the FP64 pipe stays fed on
-// the right-hand-side blocks of the solve and the residual matvec.
-template <typename T, bool TA, bool TB, bool BETA>
+// n <= 4 NQ columns: CTA = 128 rows x 4 NQ columns, 128 threads with a 4 x NQ
+// register micro-tile each (rows lane + 32 p, columns warp + 4 q): with NQ = 4,
+// 16 FMAs per 8 shared-memory loads, as in the square tile, so the FP64 pipe
+// stays fed on the right-hand-side blocks of the solve and the residual matvec.
+// NQ = 2 serves blocks of at most 8 columns (a refinement lane's) without the
+// FMAs of 8 zero columns.
+template <typename T, bool TA, bool TB, bool BETA, int NQ>
 __global__ void __launch_bounds__(128)
 gemm_n16_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, long long sA,
                 const T* __restrict__ B, int ldb, long long sB, T beta, T* C, int ldc,
                 long long sC) {
   constexpr int TBM = 128, TBK = 16, TNT = 128;
   __shared__ T As[TBK][TBM + 1];
-  __shared__ T Bs[TBK][16 + 1];
+  constexpr int NB = 4 * NQ;
+  __shared__ T Bs[TBK][NB + 1];
   const long long bz = blockIdx.z;
   A += bz * sA;
   B += bz * sB;
   C += bz * sC;
   const int i0 = blockIdx.x * TBM;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  T acc[4][4];
+  T acc[4][NQ];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < NQ; ++b) acc[a][b] = T(0);
   for (int k0 = 0; k0 < k; k0 += TBK) {
 #pragma unroll
     for (int e0 = 0; e0 < TBM * TBK; e0 += TNT) {
@@ -192,10 +195,10 @@ gemm_n16_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, 
       As[kk][i] = v;
     }
 #pragma unroll
-    for (int e0 = 0; e0 < 16 * TBK; e0 += TNT) {
+    for (int e0 = 0; e0 < NB * TBK; e0 += TNT) {
       const int e = e0 + threadIdx.x;
       int j, kk;
-      if (!TB) { kk = e % TBK; j = e / TBK; } else { j = e % 16; kk = e / 16; }
+      if (!TB) { kk = e % TBK; j = e / TBK; } else { j = e % NB; kk = e / NB; }
       const int gk = k0 + kk;
       T v = T(0);
       if (j < n && gk < k) v = TB ? B[j + (long long)gk * ldb] : B[gk + (long long)j * ldb];
@@ -204,21 +207,20 @@ gemm_n16_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, 
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TBK; ++kk) {
-      T a[4], bv[4];
+      T a[4], bv[NQ];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        a[t] = As[kk][lane + 32 * t];
-        bv[t] = Bs[kk][w + 4 * t];
-      }
+      for (int t = 0; t < 4; ++t) a[t] = As[kk][lane + 32 * t];
+#pragma unroll
+      for (int t = 0; t < NQ; ++t) bv[t] = Bs[kk][w + 4 * t];
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], bv[q], acc[p][q]);
+        for (int q = 0; q < NQ; ++q) acc[p][q] = fma(a[p], bv[q], acc[p][q]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < NQ; ++q) {
     const int gj = w + 4 * q;
     if (gj >= n) continue;
 #pragma unroll
@@ -491,12 +493,15 @@ void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA
   }
   if (n > 4 && n <= 16) {
     dim3 g((m + 127) / 128, 1, batch);
-    if (useb)
-      gemm_n16_kernel<T, TA, TB, true><<<g, 128, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
-                                                         beta, C, ldc, sC);
-    else
-      gemm_n16_kernel<T, TA, TB, false><<<g, 128, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB,
-                                                          beta, C, ldc, sC);
+#define N16_RUN(B_, NQ_)                                                                     \
+  gemm_n16_kernel<T, TA, TB, B_, NQ_><<<g, 128, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, \
+                                                        beta, C, ldc, sC)
+    if (n <= 8) {
+      if (useb) N16_RUN(true, 2); else N16_RUN(false, 2);
+    } else {
+      if (useb) N16_RUN(true, 4); else N16_RUN(false, 4);
+    }
+#undef N16_RUN
     return;
   }
   if (n <= 32) {

@@ -1180,8 +1180,7 @@ bool smem_opt_in(K kernel, size_t bytes) {
 }
 
 template <typename T>
-size_t ql_smem(int b, int r) {
-  constexpr int NBP = sizeof(T) == 8 ? 16 : 32;
+size_t ql_smem(int b, int r, int NBP) {
   // transposed panel, then the product buffers (which also hold the warps'
   // partial panel Gram matrices)
   const size_t region = std::max<size_t>((size_t)3 * NBP * r + 64 * 33,
@@ -1193,7 +1192,7 @@ template <typename T, int NBP, int RPT>
 cudaError_t launch_ql_rows(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                            long long sT, T* LB, long long sL, int b, int r, int nodes,
                            cudaStream_t st, const int* only_if) {
-  const size_t sm = ql_smem<T>(b, r);
+  const size_t sm = ql_smem<T>(b, r, NBP);
   if (!smem_opt_in(ql_basis_kernel<T, NBP, RPT>, sm)) return cudaErrorInvalidConfiguration;
   ql_basis_kernel<T, NBP, RPT><<<nodes, NT, sm, st>>>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL,
                                                       b, r, only_if);
@@ -1203,15 +1202,26 @@ cudaError_t launch_ql_rows(const T* Bsrc, int ldb_src, long long sB, T* V, long 
 template <typename T>
 cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                             long long sT, T* LB, long long sL, int b, int r, int nodes,
-                            cudaStream_t st, const int* only_if) {
-  // panel width: 16 columns in FP64, 32 in FP32; RPT panel rows per thread
-  constexpr int NBP = sizeof(T) == 8 ? 16 : 32;
+                            cudaStream_t st, const int* only_if, int panel) {
+  // panel width: 16 columns in FP64; 32 (default) or 16 in FP32.  RPT panel
+  // rows per thread.
   if (b > 3 * NT || r > 256) return cudaErrorInvalidValue;
-  if (b <= NT)
-    return launch_ql_rows<T, NBP, 1>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st, only_if);
-  if (b <= 2 * NT)
-    return launch_ql_rows<T, NBP, 2>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st, only_if);
-  return launch_ql_rows<T, NBP, 3>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st, only_if);
+#define QL_RUN(NBP_)                                                                            \
+  do {                                                                                          \
+    if (b <= NT)                                                                                \
+      return launch_ql_rows<T, NBP_, 1>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes,  \
+                                        st, only_if);                                           \
+    if (b <= 2 * NT)                                                                            \
+      return launch_ql_rows<T, NBP_, 2>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes,  \
+                                        st, only_if);                                           \
+    return launch_ql_rows<T, NBP_, 3>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes,    \
+                                      st, only_if);                                             \
+  } while (0)
+  if constexpr (sizeof(T) == 4) {
+    if (panel != 16) QL_RUN(32);
+  }
+  QL_RUN(16);
+#undef QL_RUN
 }
 
 template <typename T>
@@ -1318,6 +1328,24 @@ cudaError_t trsv_config(K kernel, int b, int nrhs, int r, bool bwd, int* CB, int
 }
 
 template <typename T>
+bool ulv_fused_fits(int b, int nrhs, int r, bool bwd) {
+  int CB, NBUF;
+  size_t sm;
+  return bwd ? trsv_config<T>(trsv_bwd_kernel<T>, b, nrhs, r, true, &CB, &NBUF, &sm) ==
+                   cudaSuccess
+             : trsv_config<T>(trsv_fwd_kernel<T>, b, nrhs, r, false, &CB, &NBUF, &sm) ==
+                   cudaSuccess;
+}
+
+template <typename T>
+bool tree_fits(int b, int nrhs, int r) {
+  int CB, NBUF;
+  size_t sm;
+  return trsv_config<T>(tree_fwd_kernel<T>, b, nrhs, r, false, &CB, &NBUF, &sm) == cudaSuccess &&
+         trsv_config<T>(tree_bwd_kernel<T>, b, nrhs, r, true, &CB, &NBUF, &sm) == cudaSuccess;
+}
+
+template <typename T>
 cudaError_t launch_ulv_fwd(const T* M, int ldm, long long sM, int b, int c, T* X, int ldx,
                            long long sX, int nrhs, T* Par, int ldpar, long long sPar, const T* V,
                            long long sV, const T* Tm, long long sT, int r, int nodes,
@@ -1403,7 +1431,7 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
 #define INST(T)                                                                                  \
   template cudaError_t launch_ql_basis<T>(const T*, int, long long, T*, long long, T*, long long,  \
                                           T*, long long, int, int, int, cudaStream_t,             \
-                                          const int*);                                             \
+                                          const int*, int);                                        \
   template cudaError_t launch_pchol<T>(T*, int, long long, int, int, T*, int, long long, double*, \
                                        int, int, int*, int, cudaStream_t);                        \
   template cudaError_t launch_trsv_fwd<T>(const T*, int, long long, int, int, T*, int, long long, \
@@ -1416,7 +1444,7 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
   template cudaError_t launch_ulv_bwd<T>(const T*, int, long long, int, int, T*, int, long long,  \
                                          int, const T*, int, long long, const T*, long long,      \
                                          const T*, long long, int, int, cudaStream_t, int);       \
-  template size_t ql_smem<T>(int, int);                                                          \
+  template size_t ql_smem<T>(int, int, int);                                                     \
   template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int, int,\
                                             int*, int, bool, cudaStream_t);                       \
   template cudaError_t launch_scatter_ss<T>(const T*, int, long long, int, int, T*, int,           \
@@ -1424,6 +1452,8 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
   template cudaError_t launch_tree_fwd<T>(const TreeLevels<T>&, int, int, int, int, int, int*,    \
                                           cudaStream_t);                                         \
   template cudaError_t launch_tree_bwd<T>(const TreeLevels<T>&, int, int, int, int, int, int*,    \
-                                          int, long long, int*, cudaStream_t);
+                                          int, long long, int*, cudaStream_t);                   \
+  template bool ulv_fused_fits<T>(int, int, int, bool);                                          \
+  template bool tree_fits<T>(int, int, int);
 INST(double)
 INST(float)

@@ -4,10 +4,12 @@
 
 // Householder QL basis completion, one CTA per node.  only_if (n flags, may be
 // null): complete only the nodes whose flag is nonzero.
+// panel: columns per register panel of the blocked QR, 16 or 32 (FP32 only;
+// 0 = the default, 32 in FP32 and 16 in FP64).
 template <typename T>
 cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long long sV, T* Tm,
                             long long sT, T* LB, long long sL, int b, int r, int nodes,
-                            cudaStream_t st, const int* only_if = nullptr);
+                            cudaStream_t st, const int* only_if = nullptr, int panel = 0);
 
 template <typename T>
 size_t pchol_smem(int b);
@@ -45,11 +47,20 @@ cudaError_t launch_ulv_bwd(const T* M, int ldm, long long sM, int b, int c, T* X
                            const T* V, long long sV, const T* Tm, long long sT, int r, int nodes,
                            cudaStream_t st, int staging = 0);
 
+// Whether a sweep launch with the Q application fused (per-level kernel, or the
+// tree kernels at block order b) fits the device's shared memory for nrhs
+// columns and rank r; where it does not, the caller applies Q by batched GEMMs
+// and runs the per-level sweeps without it.
+template <typename T>
+bool ulv_fused_fits(int b, int nrhs, int r, bool bwd);
+template <typename T>
+bool tree_fits(int b, int nrhs, int r);
+
 void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t st);
 
 // dynamic shared memory of the basis-completion kernel for a b x r basis
 template <typename T>
-size_t ql_smem(int b, int r);
+size_t ql_smem(int b, int r, int NBP);
 
 // One panel of a blocked Cholesky, for every node of a batch (stride sM): factor
 // the kb x kb diagonal block at the top of each rows x rows matrix M (ld ldm)

@@ -505,9 +505,10 @@ def cached_build(w: Workload, cache_dir: Optional[str], **kw) -> HSSMatrix:
 def batch_workloads(count: int, seed: int = 1003, n_min: int = 4096, n_max: int = 65536,
                     uniform: bool = False):
     """The batched uneven workload: `count` matrices, N log-uniform in
-    [n_min, n_max] rounded to a multiple of the leaf size (so the bisection tree
-    is uneven: L = ceil(log2(N / leaf)), leaf orders in (leaf/2, leaf]; with
-    uniform=True rounded to leaf * 2^L instead), leaf drawn from {128, 256,
+    [n_min, n_max] rounded to a multiple of the leaf size (the bisection tree has
+    L = ceil(log2(N / leaf)) levels and leaf orders in (leaf/2, leaf]; it is
+    uneven where 2^L does not divide N; with uniform=True N is rounded to
+    leaf * 2^L instead), leaf drawn from {128, 256,
     512}, rank from {32, 64, 128}, kernel half 1/(d + 1e-3) on the unit cube
     (+ N^(1/3) I), half exp(-d / 0.1) on a jittered 2-D grid (+ 1e-4 I); one
     right-hand side each."""

@@ -68,11 +68,16 @@ def test_batch_workload_family_reduced():
 
 
 def test_batch_workload_family_uneven():
-    """The batched workload as specified: N rounded to a multiple of the leaf
-    size only, so every tree is uneven (padded inside the library)."""
+    """The batched workload as specified (N rounded to a multiple of the leaf
+    size only; at these sizes 2^L divides N, so the trees come out uniform with
+    smaller leaves) together with uneven trees, where 2^L does not divide N
+    (padded inside the library)."""
     ws = I.batch_workloads(6, seed=8, n_min=512, n_max=4096)
+    ws += [I.scaled(I.WORKLOADS["cube_inv_4k"], 3000, leaf=256, rank=32),
+           I.scaled(I.WORKLOADS["grid_exp_64k"], 2500, leaf=128, rank=64),
+           I.scaled(I.WORKLOADS["cube_inv_4k"], 1100, leaf=128, rank=16)]
     mats = [I.build_hss(w) for w in ws]
-    assert not any(m.uniform for m in mats)
+    assert sum(not m.uniform for m in mats) == 3
     check_batch(mats, 1, 4)
 
 

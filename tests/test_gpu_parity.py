@@ -151,9 +151,13 @@ def test_matches_dense_cholesky_exact_rank():
     assert abs(dev.logdet() - np.linalg.slogdet(K)[1]) <= 1e-10 * abs(np.linalg.slogdet(K)[1])
 
 
-@pytest.mark.parametrize("nrhs", [1, 5, 33])
-def test_matvec(nrhs):
-    h = I.random_hss(4, 80, 24, seed=5, orthonormal=False)
+@pytest.mark.parametrize("levels,leaf,rank,nrhs", [
+    (4, 80, 24, 1), (4, 80, 24, 5), (4, 80, 24, 33),
+    # 256 leaves: the wide-level kernels with 4-, 8- and 16-column blocks
+    (8, 72, 16, 3), (8, 72, 16, 8), (8, 72, 16, 13), (8, 72, 16, 16),
+])
+def test_matvec(levels, leaf, rank, nrhs):
+    h = I.random_hss(levels, leaf, rank, seed=5, orthonormal=False)
     dev = hss.HSS(h)
     x = I.rhs(h.n, nrhs, 9)
     y = dev.matvec(hss.colmajor(x)).cpu().numpy()
@@ -290,6 +294,27 @@ def test_mixed_fp32_in_place_and_many_columns():
     assert err.max() <= 1e-10
 
 
+def test_refinement_two_lanes_and_one_lane_agree():
+    """The columns of a refinement pass split over two lanes (each lane stops on
+    its own columns' residuals) give the one-lane solution to the tolerance; a
+    serialized trace runs one lane."""
+    h = I.random_hss(4, 64, 16, seed=21, orthonormal=False)
+    dev = hss.HSS(h)
+    dev.factorize("fp32", ir_tol=1e-13)
+    b = I.rhs(h.n, 16, 8)
+    b[:, 9:] *= 1e6                     # the second lane's columns at another scale
+    x2 = dev.solve(hss.colmajor(b)).cpu().numpy()
+    it2 = dev.last_info()["ir_iters"]
+    dev.trace(True, serialize=True)
+    x1 = dev.solve(hss.colmajor(b)).cpu().numpy()
+    dev.trace(False)
+    for x in (x1, x2):
+        res = b - O.matvec(h, x)
+        assert (np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)).max() <= 1e-13
+    err = np.linalg.norm(x2 - x1, axis=0) / np.linalg.norm(x1, axis=0)
+    assert err.max() <= 1e-11 and it2 >= 1, (err, it2)
+
+
 def test_mixed_refinement_reports_no_convergence():
     h = I.random_hss(2, 32, 8, seed=3)
     dev = hss.HSS(h)
@@ -301,14 +326,17 @@ def test_mixed_refinement_reports_no_convergence():
     assert info["ir_iters"] == 2 and info["ir_resid"] < 1e-10
 
 
-@pytest.mark.parametrize("levels,leaf,rank", [(3, 100, 13), (2, 256, 32), (3, 128, 48)])
-def test_per_step_fp32_factor(levels, leaf, rank):
+@pytest.mark.parametrize("levels,leaf,rank,panel", [
+    (3, 100, 13, 0), (2, 256, 32, 0), (3, 128, 48, 0),
+    (3, 100, 13, 16), (2, 512, 128, 16), (3, 300, 40, 16),   # 16-column register panels
+])
+def test_per_step_fp32_factor(levels, leaf, rank, panel):
     """The FP32 factor against the oracle run in float32 (LAPACK sgeqrf / spotrf
     order of operations differs, so the bound is a few hundred FP32 ulps of the
-    block's scale)."""
+    block's scale), with the basis kernel's default and 16-column panels."""
     h = I.random_hss(levels, leaf, rank, seed=levels * 7 + rank, orthonormal=False)
     dev = hss.HSS(h)
-    dev.factorize("fp32")
+    dev.factorize("fp32", ql_panel=panel)
     F = O.factor(h, dtype=np.float32)
     for l in range(levels, 0, -1):
         V, T, LB, M = (dev.export(k, l) for k in ("V", "T", "LB", "M"))
@@ -521,6 +549,9 @@ def test_autotuner_choices_and_cache(prec, tmp_path):
     t = dev.tune(prec, nrhs=4, cache=cache)
     assert t["basis"] in ("householder", "cholqr") and t["schedule"] in ("async", "levels")
     assert not t["from_cache"] and 0 < t["factor_ms"] < 1e4 and 0 < t["solve_ms"] < 1e4
+    panels = t["measured"]["factor_ms_householder_panel"]
+    assert set(panels) == ({"16"} if prec == "fp64" else {"16", "32"}), t
+    assert t["ql_panel"] in (16, 32) and min(t["measured"]["factor_ms"].values()) == t["factor_ms"]
     b = I.rhs(h.n, 4, 1)
     x = dev.solve(hss.colmajor(b)).cpu().numpy()
     x_ref = O.solve(O.factor(h), b)
@@ -528,6 +559,7 @@ def test_autotuner_choices_and_cache(prec, tmp_path):
     dev2 = hss.HSS(h)
     t2 = dev2.tune(prec, nrhs=4, cache=cache)
     assert t2["from_cache"] and t2["basis"] == t["basis"] and t2["schedule"] == t["schedule"]
+    assert t2["ql_panel"] == t["ql_panel"]
     dev2.factorize(prec, basis="auto", schedule="auto")
     x2 = dev2.solve(hss.colmajor(b)).cpu().numpy()
     assert (np.linalg.norm(x2 - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)).max() <= 1e-10
@@ -549,3 +581,15 @@ def test_leaf_768_sixteen_columns(prec):
     assert err.max() <= 1e-10, err
     if prec == "fp64":
         check_end_to_end(dev, F, b, x)
+
+
+def test_ql_panel_option_checked():
+    h = I.random_hss(2, 32, 8, seed=25)
+    dev = hss.HSS(h)
+    with pytest.raises(hss.HSSError) as ei:
+        dev.factorize("fp32", ql_panel=24)
+    assert ei.value.code == -1
+    dev.factorize("fp64", ql_panel=32)     # FP64 has 16-column panels only: ignored
+    x = dev.solve(hss.colmajor(np.ones(h.n))).cpu().numpy()
+    x_ref = O.solve(O.factor(h), np.ones((h.n, 1)))
+    assert np.abs(x.reshape(-1) - x_ref.reshape(-1)).max() <= 1e-10 * np.abs(x_ref).max()
