@@ -464,7 +464,7 @@ def run_ours(args):
         tempfile.gettempdir(), f"hss_tune_{os.getpid()}.txt")
     tuning = {prec: dev.tune(prec, w.nrhs, resid, cache=tune_cache)}
     for _ in range(args.warmup):
-        dev.factorize(prec, residual=resid, basis="auto", schedule="auto")
+        dev.factorize(prec, residual=resid, basis="auto", schedule=args.schedule)
         dev.solve(b, x)
     if args.profile_step:
         # one step inside the profiler window (ncu --profile-from-start off):
@@ -472,7 +472,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         l0 = dev.launch_count()
-        dev.factorize(prec, residual=resid, basis="auto", schedule="auto")
+        dev.factorize(prec, residual=resid, basis="auto", schedule=args.schedule)
         dev.solve(b, x)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
@@ -779,6 +779,8 @@ def main():
                     help="arithmetic of the refinement residual of the mixed modes")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other precisions / residuals and the FP64 path")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "async", "levels"],
+                    help="solve schedule of --profile-step (default: the autotuner's)")
     ap.add_argument("--profile-step", action="store_true",
                     help="run W warm-up steps, then one step between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and exit")

@@ -143,8 +143,8 @@ struct hss_s {
   // launch accounting and the optional per-launch event log
   long long launches = 0;
   int tracing = 0;
-  int serialize = 0;                   // run the basis chain, the matvec and the
-                                       // refinement on the caller's stream only
+  int serialize = 0;                   // run the basis chain, the matvec and both
+                                       // refinement lanes on the caller's stream only
   struct Rec {
     int kind;
     double flops;
@@ -950,10 +950,9 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
       ldb = n;
     }
     // two lanes over the columns when there are two columns or more (the pair
-    // residual's split buffers are shared, and a serialized trace times one
-    // stream: one lane)
-    const int lanes = (nc >= 2 && h->ir_lanes == 2 && h->residual == HSS_RESIDUAL_FP64 &&
-                       !h->serialize) ? 2 : 1;
+    // residual's split buffers are shared: one lane); a serialized trace runs
+    // both lanes' launches on the caller's stream, one after the other
+    const int lanes = (nc >= 2 && h->ir_lanes == 2 && h->residual == HSS_RESIDUAL_FP64) ? 2 : 1;
     IrLane lane[2];
     lane[0].g = 0;
     lane[0].c0 = 0;
@@ -962,7 +961,7 @@ int solve_ir(hss_s* h, const double* b, double* x, int nrhs, int ld, cudaStream_
     lane[1].g = 1;
     lane[1].c0 = lane[0].nc;
     lane[1].nc = nc - lane[0].nc;
-    lane[1].ls = h->lane[1].st;
+    lane[1].ls = h->serialize ? st : h->lane[1].st;
     // residual r = b - A x of a lane, its norms and the status word to the host
     auto residual_step = [&](IrLane& q) -> int {
       const long long o = (long long)q.c0 * n;

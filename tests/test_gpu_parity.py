@@ -296,8 +296,9 @@ def test_mixed_fp32_in_place_and_many_columns():
 
 def test_refinement_two_lanes_and_one_lane_agree():
     """The columns of a refinement pass split over two lanes (each lane stops on
-    its own columns' residuals) give the one-lane solution to the tolerance; a
-    serialized trace runs one lane."""
+    its own columns' residuals, the lanes on two streams, or one after the other
+    on the caller's stream under a serialized trace) give the solution of
+    one-column solves (one lane) to the tolerance."""
     h = I.random_hss(4, 64, 16, seed=21, orthonormal=False)
     dev = hss.HSS(h)
     dev.factorize("fp32", ir_tol=1e-13)
@@ -306,11 +307,14 @@ def test_refinement_two_lanes_and_one_lane_agree():
     x2 = dev.solve(hss.colmajor(b)).cpu().numpy()
     it2 = dev.last_info()["ir_iters"]
     dev.trace(True, serialize=True)
-    x1 = dev.solve(hss.colmajor(b)).cpu().numpy()
+    xs = dev.solve(hss.colmajor(b)).cpu().numpy()
     dev.trace(False)
-    for x in (x1, x2):
+    x1 = np.stack([dev.solve(hss.colmajor(b[:, j])).cpu().numpy().reshape(-1)
+                   for j in range(16)], axis=1)
+    for x in (x1, x2, xs):
         res = b - O.matvec(h, x)
         assert (np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)).max() <= 1e-13
+    assert np.array_equal(x2, xs)
     err = np.linalg.norm(x2 - x1, axis=0) / np.linalg.norm(x1, axis=0)
     assert err.max() <= 1e-11 and it2 >= 1, (err, it2)
 
