@@ -710,6 +710,66 @@ def run_sweep(args):
     return 0
 
 
+def run_large(args):
+    """The largest workload's shape on one GPU: N = 2^21, leaf 1024, rank 256, 11
+    levels, 4 right-hand sides, mixed factor (FP32, TF32 x3, BF16 x3; the
+    autotuner's basis, panel and schedule) refined to 1e-12 with the FP64
+    residual, against the FP64 HSS matvec of the result.  The generators are
+    seeded random ones with that shape, built on the GPU (orthonormal nested
+    bases, SPD by a diagonal shift, random_hss_device): the kernel-valued
+    construction of this N is O(N^2 r) on the host.  One JSON line."""
+    import torch
+    from paper_2311_00921_gb300 import hss, inputs as I
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    L, leaf, r, nrhs = 11, 1024, 256, 4
+    t0 = time.time()
+    shape, D, U, E, S, shift = I.random_hss_device(L, leaf, r, seed=1004)
+    dev = hss.HSS.from_device(shape, D, U, E, S)
+    del D, U, E, S
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    n = shape[0]
+    bh = I.rhs(n, nrhs, 1005)
+    b = hss.colmajor(bh)
+    x = torch.empty_like(b)
+    fl = factor_flops(L, leaf, r) + solve_flops(L, leaf, r, nrhs)
+    out = {"metric": "HSS-ULV factor+solve at N=2^21, leaf 1024, rank 256 (1 GPU)",
+           "n": n, "leaf": leaf, "rank": r, "levels": L, "nrhs": nrhs,
+           "data": "seeded random generators of this shape built on the GPU (SPD by shift "
+                   f"{shift:g}); the exponential-covariance construction is not run at this N",
+           "generation_s": gen_s}
+    for prec in args.large_precisions.split(","):
+        tune = dev.tune(prec, nrhs, "fp64")
+        for _ in range(args.warmup):
+            dev.factorize(prec, basis="auto", schedule="auto")
+            dev.solve(b, x)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fms = sms = 0.0
+        for _ in range(args.steps):
+            e[0].record()
+            dev.factorize(prec, basis="auto", schedule="auto")
+            e[1].record()
+            dev.solve(b, x)
+            e[2].record()
+            torch.cuda.synchronize()
+            fms += e[0].elapsed_time(e[1])
+            sms += e[1].elapsed_time(e[2])
+        fms, sms = fms / args.steps, sms / args.steps
+        info = dev.last_info()
+        res = b - dev.matvec(x)
+        rel = (torch.linalg.vector_norm(res, dim=0) / torch.linalg.vector_norm(b, dim=0)).max()
+        out[prec] = {"factor_ms": fms, "solve_ms": sms, "ms_per_step": fms + sms,
+                     "tflops": fl / ((fms + sms) / 1e3) / 1e12, "ir_iterations": info["ir_iters"],
+                     "max_rel_residual_fp64_matvec": rel.item(),
+                     "autotune": {k: tune[k] for k in ("basis", "ql_panel", "schedule", "staging")}}
+    out["device_memory_gb"] = torch.cuda.max_memory_allocated() / 1e9
+    free, total = torch.cuda.mem_get_info()
+    out["device_memory_in_use_gb"] = (total - free) / 1e9
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_e2e(args, h, w, b_host, prec, fl_step, world, dist, tune_cache):
     """One user call sequence per step from pinned host memory: create the object
     (H2D of the generators), factor (hss_tune with the cached choice of the
@@ -793,6 +853,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--n", type=int, default=0,
                     help="scale the workload to this order (same leaf, rank, kernel)")
+    ap.add_argument("--large", action="store_true",
+                    help="N = 2^21, leaf 1024, rank 256 with random generators of that shape")
+    ap.add_argument("--large-precisions", default="fp32,tf32",
+                    help="factor precisions of --large (comma-separated)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -804,6 +868,8 @@ def main():
         return run_batch(args)
     if args.sweep:
         return run_sweep(args)
+    if args.large:
+        return run_large(args)
     return run_ours(args)
 
 

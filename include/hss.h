@@ -76,8 +76,10 @@ typedef enum {
 
 typedef struct {
   int32_t n;      /* matrix order: leaf * 2^levels, or the sum of node_sizes */
-  int32_t leaf;   /* leaf block order (1 .. 768); with node_sizes, the largest leaf
-                     order */
+  int32_t leaf;   /* leaf block order (1 .. 1024); with node_sizes, the largest leaf
+                     order.  Above 768 the FP64 factorization takes rank <= 176 (the
+                     basis kernel's shared memory; hss_factorize reports
+                     HSS_ERR_INVALID_ARG beyond); the FP32 one any rank. */
   int32_t rank;   /* rank of every basis (1 .. min(leaf, 256)); with node_sizes the
                      largest rank, see below */
   int32_t levels; /* L >= 1 */
@@ -185,7 +187,7 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream);
  * matvec in the arithmetic hss_options.residual selects) and synchronizes once per
  * iteration; it returns HSS_ERR_NO_CONVERGENCE if ir_max_it is reached (x then
  * holds the last iterate).  Errors: NOT_FACTORIZED, INVALID_ARG, CUDA.
- * Every leaf order up to 768 is solved in every precision (the sweeps stage their
+ * Every leaf order up to 1024 is solved in every precision (the sweeps stage their
  * panels in as much shared memory as the device grants). */
 int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, void* stream);
 

@@ -1088,7 +1088,7 @@ int hss_create(const hss_shape* shape, const double* D, const double* U, const d
   if (!shape || !out || !D || !U || !S) return HSS_ERR_INVALID_ARG;
   *out = nullptr;
   const int L = shape->levels, leaf = shape->leaf, r = shape->rank;
-  if (L < 1 || L > 24 || leaf < 1 || leaf > 768 || r < 1 || r > leaf || r > 256)
+  if (L < 1 || L > 24 || leaf < 1 || leaf > 1024 || r < 1 || r > leaf || r > 256)
     return HSS_ERR_INVALID_ARG;
   if (L >= 2 && !E) return HSS_ERR_INVALID_ARG;
   // an uneven tree: its generators embedded in the uniform (leaf, rank) ones

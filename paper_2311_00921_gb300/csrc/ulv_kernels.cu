@@ -1204,8 +1204,9 @@ cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long
                             long long sT, T* LB, long long sL, int b, int r, int nodes,
                             cudaStream_t st, const int* only_if, int panel) {
   // panel width: 16 columns in FP64; 32 (default) or 16 in FP32.  RPT panel
-  // rows per thread.
-  if (b > 3 * NT || r > 256) return cudaErrorInvalidValue;
+  // rows per thread (b <= RPT NT); four rows a thread hold a 16-column panel
+  // only, so the register panel stays within the register file.
+  if (b > 4 * NT || r > 256) return cudaErrorInvalidValue;
 #define QL_RUN(NBP_)                                                                            \
   do {                                                                                          \
     if (b <= NT)                                                                                \
@@ -1214,11 +1215,14 @@ cudaError_t launch_ql_basis(const T* Bsrc, int ldb_src, long long sB, T* V, long
     if (b <= 2 * NT)                                                                            \
       return launch_ql_rows<T, NBP_, 2>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes,  \
                                         st, only_if);                                           \
-    return launch_ql_rows<T, NBP_, 3>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes,    \
-                                      st, only_if);                                             \
+    if (b <= 3 * NT || NBP_ > 16)                                                               \
+      return launch_ql_rows<T, NBP_, 3>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes,  \
+                                        st, only_if);                                           \
+    return launch_ql_rows<T, 16, 4>(Bsrc, ldb_src, sB, V, sV, Tm, sT, LB, sL, b, r, nodes, st,  \
+                                    only_if);                                                   \
   } while (0)
   if constexpr (sizeof(T) == 4) {
-    if (panel != 16) QL_RUN(32);
+    if (panel != 16 && b <= 3 * NT) QL_RUN(32);
   }
   QL_RUN(16);
 #undef QL_RUN

@@ -201,6 +201,22 @@ class HSS:
         self._h = out
         self.precision = None
 
+    @classmethod
+    def from_device(cls, shape, D, U, E, S):
+        """An HSS object from generators already in device memory: shape = (n,
+        leaf, rank, levels) of a uniform tree, D, U, E, S float64 CUDA tensors in
+        the packed layout of hss_create (copied device to device)."""
+        self = cls.__new__(cls)
+        n, leaf, r, L = shape
+        sh = Shape(n, leaf, r, L)
+        out = _p()
+        _check(load().hss_create(ctypes.byref(sh), D.data_ptr(), U.data_ptr(), E.data_ptr(),
+                                 S.data_ptr(), 1, ctypes.byref(out)), "hss_create")
+        self._h = out
+        self.n, self.levels, self.rank, self.leaf = n, L, r, leaf
+        self.precision = None
+        return self
+
     def close(self):
         if getattr(self, "_h", None):
             load().hss_destroy(self._h)

@@ -453,6 +453,51 @@ def random_hss(levels: int, leaf: int, rank: int, seed: int, *,
                      D=D, U=U, E=E, S=S)
 
 
+def random_hss_device(levels: int, leaf: int, rank: int, seed: int, device="cuda"):
+    """Random-generator HSS matrix built on the GPU with torch, for shapes whose
+    host construction is out of reach (N = 2^21, leaf 1024, rank 256: 25 GB of
+    generators).  Returns (shape, D, U, E, S, shift): float64 device tensors in
+    the packed column-major layout of hss_create (D 2^L blocks b x b, U 2^L
+    blocks b x r, E levels 1 .. L-1 of 2^l blocks 2r x r, S levels 1 .. L of
+    2^(l-1) blocks r x r).
+
+    U and E have orthonormal columns (QR of Gaussian blocks), so every nested
+    basis is orthonormal; S is Gaussian / sqrt(r) (2-norm about 2) and D_i =
+    sym(G_i) / sqrt(2b) + shift I.  The off-diagonal part's norm is at most
+    sum over levels of max ||S||_2 <= 2.5 L, so shift = 2 (2.5 L) + 3 keeps the
+    matrix SPD with condition number about 3.  Seeded: the same (levels, leaf,
+    rank, seed) gives the same matrix on any GPU of the same arithmetic."""
+    import torch
+    L, b, r = levels, leaf, rank
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = torch.float64
+    shift = 2.0 * 2.5 * L + 3.0
+
+    def orthonormal(count, m, k):
+        out = torch.empty((count, k, m), dtype=f64, device=device)   # column-major m x k
+        for c0 in range(0, count, 256):
+            c1 = min(count, c0 + 256)
+            q, _ = torch.linalg.qr(torch.randn((c1 - c0, m, k), generator=g, dtype=f64,
+                                               device=device))
+            out[c0:c1] = q.transpose(1, 2)
+        return out
+
+    D = torch.empty((2 ** L, b, b), dtype=f64, device=device)
+    for c0 in range(0, 2 ** L, 256):
+        c1 = min(2 ** L, c0 + 256)
+        G = torch.randn((c1 - c0, b, b), generator=g, dtype=f64, device=device)
+        D[c0:c1] = (G + G.transpose(1, 2)) / (2.0 * math.sqrt(2.0 * b))
+        D[c0:c1].diagonal(dim1=1, dim2=2).add_(shift)
+        del G
+    U = orthonormal(2 ** L, b, r)
+    E = (torch.cat([orthonormal(2 ** l, 2 * r, r).reshape(-1) for l in range(1, L)])
+         if L >= 2 else torch.zeros(1, dtype=f64, device=device))
+    S = torch.cat([(torch.randn((2 ** (l - 1), r, r), generator=g, dtype=f64, device=device)
+                    / math.sqrt(r)).reshape(-1) for l in range(1, L + 1)])
+    return (b << L, b, r, L), D.reshape(-1), U.reshape(-1), E, S, shift
+
+
 def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
     """N(0,1) right-hand sides, column-major n x nrhs as a Fortran-ordered array."""
     rng = np.random.default_rng(seed)

@@ -597,3 +597,53 @@ def test_ql_panel_option_checked():
     x = dev.solve(hss.colmajor(np.ones(h.n))).cpu().numpy()
     x_ref = O.solve(O.factor(h), np.ones((h.n, 1)))
     assert np.abs(x.reshape(-1) - x_ref.reshape(-1)).max() <= 1e-10 * np.abs(x_ref).max()
+
+
+# ---------------------------------------------------------------- leaf 1024
+def test_leaf_1024_rank_256_mixed_against_oracle():
+    """The node shape of the largest workload (leaf 1024, rank 256: the exponential
+    covariance on the unit cube, N scaled to 8,192, 3 levels): the FP32 factor
+    per step against the oracle's float32 factor (basis completion with 16-column
+    panels and four rows a thread, L^RR, Â^SS), then FP32, TF32 x3 and BF16 x3
+    factors refined to 1e-12 with the FP64 residual against the FP64 oracle's
+    solution.  The FP64 factor at this rank exceeds the basis kernel's shared
+    memory and is refused."""
+    w = I.scaled(I.WORKLOADS["cube_exp_2m"], 8192)
+    h = I.build_hss(w)
+    assert (h.leaf, h.rank, h.levels) == (1024, 256, 3)
+    dev = hss.HSS(h)
+    dev.factorize("fp32")
+    F32 = O.factor(h, dtype=np.float32)
+    for l in range(h.levels, 0, -1):
+        V, T, LB, M = (dev.export(k, l) for k in ("V", "T", "LB", "M"))
+        for i in range(2 ** l):
+            b, r = V.shape[1], V.shape[2]
+            c = b - r
+            check_close(q_from_vt(V[i], T[i]), F32.Q[l][i].astype(np.float64), 2e-4,
+                        f"Q32 l={l} i={i}")
+            check_close(LB[i], F32.LB[l][i].astype(np.float64), 2e-4, f"L_B32 l={l} i={i}")
+            check_close(np.tril(M[i][:c, :c]), F32.LRR[l][i].astype(np.float64), 1e-3,
+                        f"L^RR32 l={l} i={i}")
+            check_close(np.tril(M[i][c:, c:]), np.tril(F32.SS[l][i]).astype(np.float64), 1e-3,
+                        f"SS32 l={l} i={i}")
+    b = I.rhs(h.n, 4, w.seed + 1)
+    x_ref = O.solve(O.factor(h), b)
+    for prec in ("fp32", "tf32", "bf16"):
+        dev.factorize(prec)
+        x = dev.solve(hss.colmajor(b)).cpu().numpy()
+        res = b - O.matvec(h, x)
+        assert (np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)).max() <= 1e-12, prec
+        err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+        assert err.max() <= 1e-10, (prec, err)
+    with pytest.raises(hss.HSSError) as ei:
+        dev.factorize("fp64")
+    assert ei.value.code == -1
+
+
+def test_leaf_1024_fp64_per_step():
+    """FP64 at leaf 1024 with rank 160 (within the basis kernel's shared memory):
+    every step of every node and the solution against the oracle."""
+    h = I.random_hss(2, 1024, 160, seed=1024, orthonormal=False)
+    dev, F, b, x = run_both(h, 16)
+    check_steps(dev, F, h)
+    check_end_to_end(dev, F, b, x)
