@@ -154,6 +154,10 @@ typedef struct {
                           default (32 in FP32).  With basis = HSS_BASIS_AUTO the
                           choice of hss_tune is used instead.  Other values:
                           HSS_ERR_INVALID_ARG. */
+  int32_t ir_lanes;    /* refinement lanes of a mixed solve with the FP64 residual: 1 or 2;
+                          0 = the choice of hss_tune under schedule = HSS_SCHEDULE_AUTO,
+                          else 1.  Other values: HSS_ERR_INVALID_ARG. */
+  int32_t reserved;    /* 0 */
 } hss_options;
 
 /* Create a device-resident HSS object from its generators (format above).
@@ -186,7 +190,12 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream);
  * refinement with an FP64 iterate, update and stopping test (residual by the HSS
  * matvec in the arithmetic hss_options.residual selects) and synchronizes once per
  * iteration; it returns HSS_ERR_NO_CONVERGENCE if ir_max_it is reached (x then
- * holds the last iterate).  Errors: NOT_FACTORIZED, INVALID_ARG, CUDA.
+ * holds the last iterate).  With the FP64 residual and the autotuner's choice
+ * (schedule = HSS_SCHEDULE_AUTO after hss_tune) a pass of columns may run on two
+ * lanes (streams) of half the columns each, one lane's FP32 sweeps beside the
+ * other's FP64 matvec; each lane stops on its own columns, so a column's
+ * result does not depend on the split.  Errors: NOT_FACTORIZED, INVALID_ARG,
+ * CUDA.
  * Every leaf order up to 1024 is solved in every precision (the sweeps stage their
  * panels in as much shared memory as the device grants). */
 int hss_solve(hss_t h, const double* b, double* x, int32_t nrhs, int32_t ld, void* stream);
@@ -249,8 +258,8 @@ int hss_matvec_noalloc(const hss_shape* shape, const double* D, const double* U,
  * panel holds more of the basis in registers, the narrower one lets two CTAs
  * share an SM), the schedule of the solve's upper levels, the panel staging of
  * the solve's sweep kernels (0 = the largest shared-memory panels, 1 = the
- * panels that let the fewest waves of CTAs cover a level), and the measured
- * times of the chosen configuration. */
+ * panels that let the fewest waves of CTAs cover a level), the refinement
+ * lanes of a mixed solve, and the measured times of the chosen configuration. */
 typedef struct {
   int32_t basis;      /* hss_basis_method */
   int32_t schedule;   /* hss_schedule */
@@ -261,9 +270,11 @@ typedef struct {
   double factor_ms_by_basis[2];        /* every candidate measured: [basis method] */
   double solve_ms_by_config[2][2];     /* [schedule][staging]; 0 where not measured */
   int32_t ql_panel;                    /* 16 or 32 */
-  int32_t reserved;
+  int32_t ir_lanes;                    /* refinement lanes, 1 or 2 (see hss_solve) */
   double factor_ms_by_panel[2];        /* Householder basis with 16 / 32-column panels;
                                           0 where not measured (FP64 has 16 only) */
+  double solve_ms_by_lanes[2];         /* best solve with 1 / 2 refinement lanes; 0 where
+                                          not measured */
 } hss_tuning;
 
 /* Autotuner: for the object's shape and the arithmetic of opt (precision,

@@ -117,7 +117,7 @@ struct hss_s {
   int staging = 0;                     // panel staging of the sweep kernels (see launch_ulv_fwd)
   int tuned = 0;                       // hss_tune has chosen the following
   int tuned_basis = HSS_BASIS_HOUSEHOLDER, tuned_schedule = HSS_SCHEDULE_ASYNC, tuned_staging = 0;
-  int tuned_panel = 0;
+  int tuned_panel = 0, tuned_lanes = 1;
   int ql_panel = 0;                    // register panel of the Householder basis kernel (0 = default)
 
   // pair-of-FP32 generators (hi parts are the FP32 factor's converted copies)
@@ -135,7 +135,8 @@ struct hss_s {
   cudaEvent_t ev_ir_fork = nullptr, ev_ir_join = nullptr;
   double* hnorm = nullptr;             // pinned host: |b|, |r| of the kSolveCols columns, then
                                        // each refinement lane's status words (8 ints a lane)
-  int ir_lanes = 2;                    // 1: one lane (no overlap)
+  int ir_lanes = 1;                    // refinement lanes (2: one lane's FP32 sweeps beside
+                                       // the other's FP64 matvec), the tuner's choice
   double* zq64 = nullptr;              // merge scratch of the basis chain (n_L/2 x r x r)
   float* zq32 = nullptr;
   int ir_iters = 0;
@@ -398,7 +399,7 @@ double trsv_flops(int b, int c, int nrhs) { return ((double)c * c + 2.0 * (b - c
 double qapply_flops(int b, int r, int nrhs) { return (4.0 * b * r + 2.0 * r * r) * nrhs; }
 
 enum { SPLIT_D = 1, SPLIT_U = 2, SPLIT_E = 4, SPLIT_S = 8, SPLIT_ALL = 15 };
-cudaError_t split_generators(hss_s* h, cudaStream_t st, int which);
+cudaError_t split_generators(hss_s* h, cudaStream_t st, int which, bool lo);
 
 // levels L .. 1 of Alg. 2; leaves the merged root block in f.lv[0].A.
 // Two chains: the basis chain (basis completion of level l, then the merge's
@@ -416,7 +417,9 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
   if (cudaEventRecord(h->ev_start, st) != cudaSuccess) return HSS_ERR_CUDA;
   if (cudaStreamWaitEvent(qs, h->ev_start, 0) != cudaSuccess) return HSS_ERR_CUDA;
   if constexpr (std::is_same<T, float>::value) {
-    if (split_d && split_generators(h, st, SPLIT_D) != cudaSuccess) return HSS_ERR_CUDA;
+    if (split_d && split_generators(h, st, SPLIT_D, h->residual == HSS_RESIDUAL_PAIR32) !=
+                       cudaSuccess)
+      return HSS_ERR_CUDA;
   }
   // basis chain
   for (int l = L; l >= 1; --l) {
@@ -580,12 +583,15 @@ int factorize(hss_s* h, int prec, cudaStream_t st) {
   } else {
     Factor<float>& f = h->f32;
     // the generators in FP32 (part of every factorization), with their
-    // low-order FP32 parts for the pair-arithmetic residual: U, E and S before
-    // the basis chain starts, D (the large one) on the main chain after it
-    HSS_TRY(split_generators(h, st, SPLIT_U | SPLIT_E | SPLIT_S));
+    // low-order FP32 parts when the residual is the pair-arithmetic one: U, E
+    // and S before the basis chain starts, D (the large one) on the main chain
+    // after it
+    const bool lo = h->residual == HSS_RESIDUAL_PAIR32;
+    h->pairs_valid = 0;
+    HSS_TRY(split_generators(h, st, SPLIT_U | SPLIT_E | SPLIT_S, lo));
     int rc = factor_levels<float>(h, f, h->zq32, st, /*split_d=*/true);
     if (rc) return rc;
-    h->pairs_valid = 1;
+    h->pairs_valid = lo ? 1 : 0;
     {   // the root block goes to FP64 for the root Cholesky
       Launch k(h, HSS_K_OTHER, 0.0, st);
       launch_f32_to_f64(f.lv[0].A, h->R0, 4LL * r * r, st);
@@ -803,30 +809,30 @@ int matvec_fp64(hss_s* h, const double* x, int ldx, double* y, int ldy, int nrhs
   return HSS_OK;
 }
 
-// hi = fl32(g) into the FP32 factor's generator copies, lo = fl32(g - hi);
-// `which` selects D, U, E, S (SPLIT_*)
-cudaError_t split_generators(hss_s* h, cudaStream_t st, int which) {
+// hi = fl32(g) into the FP32 factor's generator copies and, with `lo`, the
+// low-order parts fl32(g - hi) of the pair representation (used only by the
+// pair-arithmetic matvec); `which` selects D, U, E, S (SPLIT_*)
+cudaError_t split_generators(hss_s* h, cudaStream_t st, int which, bool lo) {
   const int L = h->L, r = h->rank;
   Factor<float>& f = h->f32;
   const long long nL = 1LL << L;
   cudaError_t e = cudaSuccess;
   if (which & SPLIT_D) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
-    e = launch_df_split(h->D, f.Dc, h->Dl, nL * h->leaf * h->leaf, st);
+    e = launch_df_split(h->D, f.Dc, lo ? h->Dl : nullptr, nL * h->leaf * h->leaf, st);
   }
   if (e == cudaSuccess && (which & SPLIT_U)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
-    e = launch_df_split(h->U, f.Uc, h->Ul, nL * h->leaf * r, st);
+    e = launch_df_split(h->U, f.Uc, lo ? h->Ul : nullptr, nL * h->leaf * r, st);
   }
   if (e == cudaSuccess && h->esz && (which & SPLIT_E)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
-    e = launch_df_split(h->E, f.Ec, h->El, h->esz, st);
+    e = launch_df_split(h->E, f.Ec, lo ? h->El : nullptr, h->esz, st);
   }
   if (e == cudaSuccess && (which & SPLIT_S)) {
     Launch k(h, HSS_K_OTHER, 0.0, st);
-    e = launch_df_split(h->S, f.Sc, h->Sl, h->ssz, st);
+    e = launch_df_split(h->S, f.Sc, lo ? h->Sl : nullptr, h->ssz, st);
   }
-  if (e == cudaSuccess && which == SPLIT_ALL) h->pairs_valid = 1;
   return e;
 }
 
@@ -1209,6 +1215,7 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     return HSS_ERR_INVALID_ARG;
   if (opt && opt->ql_panel != 0 && opt->ql_panel != 16 && opt->ql_panel != 32)
     return HSS_ERR_INVALID_ARG;
+  if (opt && (opt->ir_lanes < 0 || opt->ir_lanes > 2)) return HSS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->factorized = 0;
   if (prec != HSS_FP64) {
@@ -1227,12 +1234,14 @@ int hss_factorize(hss_t h, const hss_options* opt, void* stream) {
     const bool sauto = opt->schedule == HSS_SCHEDULE_AUTO;
     h->schedule = sauto ? (h->tuned ? h->tuned_schedule : HSS_SCHEDULE_ASYNC) : opt->schedule;
     h->staging = sauto && h->tuned ? h->tuned_staging : 0;
+    h->ir_lanes = opt->ir_lanes ? opt->ir_lanes : (sauto && h->tuned ? h->tuned_lanes : 1);
   } else {
     h->wait_budget = 0;
     h->basis_method = HSS_BASIS_HOUSEHOLDER;
     h->ql_panel = 0;
     h->schedule = HSS_SCHEDULE_ASYNC;
     h->staging = 0;
+    h->ir_lanes = 1;
   }
   h->use_tc = (prec == HSS_MIXED_TF32 || prec == HSS_MIXED_BF16) ? 1 : 0;
   h->tc_mode = (prec == HSS_MIXED_BF16) ? TcMode::BF16x3 : TcMode::TF32x3;
@@ -1341,7 +1350,10 @@ int hss_matvec_pair(hss_t h, const double* x, double* y, int32_t nrhs, int32_t l
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->last_stream = st;
-  if (!h->pairs_valid && split_generators(h, st, SPLIT_ALL) != cudaSuccess) return HSS_ERR_CUDA;
+  if (!h->pairs_valid) {
+    if (split_generators(h, st, SPLIT_ALL, true) != cudaSuccess) return HSS_ERR_CUDA;
+    h->pairs_valid = 1;
+  }
   if (h->uneven)
     return on_padded(h, x, y, nrhs, ld, kSolveCols, st, [&](const double* in, double* out, int nc) {
       return matvec_pair(h, in, h->n, out, h->n, nc, st);
@@ -1380,9 +1392,11 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
       while (fgets(line, sizeof line, f)) {
         if (strncmp(line, key, kl) != 0 || line[kl] != ' ') continue;
         hss_tuning t{};
-        if (sscanf(line + kl, " basis %d panel %d schedule %d staging %d factor_ms %lf solve_ms %lf",
-                   &t.basis, &t.ql_panel, &t.schedule, &t.staging, &t.factor_ms,
-                   &t.solve_ms) == 6 &&
+        if (sscanf(line + kl,
+                   " basis %d panel %d schedule %d staging %d lanes %d factor_ms %lf solve_ms %lf",
+                   &t.basis, &t.ql_panel, &t.schedule, &t.staging, &t.ir_lanes, &t.factor_ms,
+                   &t.solve_ms) == 7 &&
+            (t.ir_lanes == 1 || t.ir_lanes == 2) &&
             t.basis >= HSS_BASIS_HOUSEHOLDER && t.basis <= HSS_BASIS_CHOLQR &&
             (t.ql_panel == 16 || t.ql_panel == 32) &&
             t.schedule >= HSS_SCHEDULE_ASYNC && t.schedule <= HSS_SCHEDULE_LEVELS &&
@@ -1466,20 +1480,34 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
       h->tuned = 0;
     }
     best.solve_ms = 1e30;
-    for (int sched = HSS_SCHEDULE_ASYNC; rc == HSS_OK && sched <= HSS_SCHEDULE_LEVELS; ++sched) {
-      for (int stg = 0; rc == HSS_OK && stg <= 1; ++stg) {
-        h->schedule = sched;
-        h->staging = stg;
-        double ms = 0.0;
-        rc = timed([&] { return hss_solve(h, b, x, nc, h->n_user, st); }, &ms);
-        if (rc == HSS_OK) best.solve_ms_by_config[sched][stg] = ms;
-        if (rc == HSS_OK && ms < best.solve_ms) {
-          best.solve_ms = ms;
-          best.schedule = sched;
-          best.staging = stg;
+    // refinement lanes: two only where they apply (a mixed factor with the FP64
+    // residual and at least two columns)
+    const int max_lanes =
+        (o.precision != HSS_FP64 && o.residual == HSS_RESIDUAL_FP64 && nc >= 2) ? 2 : 1;
+    for (int lanes = 1; rc == HSS_OK && lanes <= max_lanes; ++lanes) {
+      h->ir_lanes = lanes;
+      double lane_best = 1e30;
+      for (int sched = HSS_SCHEDULE_ASYNC; rc == HSS_OK && sched <= HSS_SCHEDULE_LEVELS;
+           ++sched) {
+        for (int stg = 0; rc == HSS_OK && stg <= 1; ++stg) {
+          h->schedule = sched;
+          h->staging = stg;
+          double ms = 0.0;
+          rc = timed([&] { return hss_solve(h, b, x, nc, h->n_user, st); }, &ms);
+          if (rc != HSS_OK) break;
+          lane_best = std::min(lane_best, ms);
+          if (lanes == 1) best.solve_ms_by_config[sched][stg] = ms;
+          if (ms < best.solve_ms) {
+            best.solve_ms = ms;
+            best.schedule = sched;
+            best.staging = stg;
+            best.ir_lanes = lanes;
+          }
         }
       }
+      if (rc == HSS_OK) best.solve_ms_by_lanes[lanes - 1] = lane_best;
     }
+    h->ir_lanes = 1;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
@@ -1487,9 +1515,11 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
     if (rc) return rc;
     if (cache_path) {
       if (FILE* f = fopen(cache_path, "a")) {
-        fprintf(f, "%s basis %d panel %d schedule %d staging %d factor_ms %.4f solve_ms %.4f\n",
-                key, best.basis, best.ql_panel, best.schedule, best.staging, best.factor_ms,
-                best.solve_ms);
+        fprintf(f,
+                "%s basis %d panel %d schedule %d staging %d lanes %d factor_ms %.4f "
+                "solve_ms %.4f\n",
+                key, best.basis, best.ql_panel, best.schedule, best.staging, best.ir_lanes,
+                best.factor_ms, best.solve_ms);
         fclose(f);
       }
     }
@@ -1499,6 +1529,7 @@ int hss_tune(hss_t h, const hss_options* opt, int32_t nrhs, const char* cache_pa
   h->tuned_panel = best.ql_panel;
   h->tuned_schedule = best.schedule;
   h->tuned_staging = best.staging;
+  h->tuned_lanes = best.ir_lanes;
   o.basis = HSS_BASIS_AUTO;
   o.schedule = HSS_SCHEDULE_AUTO;
   const int rc = hss_factorize(h, &o, st);

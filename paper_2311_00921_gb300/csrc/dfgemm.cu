@@ -62,15 +62,36 @@ HSS_DEVINL double pow2_inv_scale(const double* colnorm, int j) {
   return ldexp(1.0, -ilogb(v));
 }
 
+// hi = fl32(a), lo = fl32(a - hi) (lo may be null: the conversion only).  Four
+// elements a thread per step with 16-byte loads and stores where the three
+// arrays are 16-byte aligned (the arena's sub-buffers are), so that the pass
+// runs at the HBM rate; the first elements up to that alignment and the tail
+// one at a time.
 __global__ void df_split_kernel(const double* __restrict__ a, float* __restrict__ hi,
-                                float* __restrict__ lo, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+                                float* __restrict__ lo, long long n, long long head) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  auto one = [&](long long i) {
     const double v = a[i];
     const float h = __double2float_rn(v);
     hi[i] = h;
-    lo[i] = __double2float_rn(v - (double)h);
+    if (lo) lo[i] = __double2float_rn(v - (double)h);
+  };
+  for (long long i = tid; i < head; i += stride) one(i);
+  const long long nv = (n - head) / 4;
+  const double2* a2 = reinterpret_cast<const double2*>(a + head);
+  float4* h4 = reinterpret_cast<float4*>(hi + head);
+  float4* l4 = lo ? reinterpret_cast<float4*>(lo + head) : nullptr;
+  for (long long q = tid; q < nv; q += stride) {
+    const double2 u = a2[2 * q], w = a2[2 * q + 1];
+    const float4 h = make_float4(__double2float_rn(u.x), __double2float_rn(u.y),
+                                 __double2float_rn(w.x), __double2float_rn(w.y));
+    h4[q] = h;
+    if (l4)
+      l4[q] = make_float4(__double2float_rn(u.x - (double)h.x), __double2float_rn(u.y - (double)h.y),
+                          __double2float_rn(w.x - (double)h.z), __double2float_rn(w.y - (double)h.w));
   }
+  for (long long i = head + 4 * nv + tid; i < n; i += stride) one(i);
 }
 
 __global__ void df_split_cols_kernel(const double* __restrict__ a, int lda, int m, int nc,
@@ -230,8 +251,18 @@ void dispatch_df(bool transA, bool acc, bool out64, int m, int n, int k, const f
 
 cudaError_t launch_df_split(const double* a, float* hi, float* lo, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
-  df_split_kernel<<<(int)blocks, 256, 0, st>>>(a, hi, lo, n);
+  // elements before a (and hi, lo) reach 16-byte alignment together; one at a
+  // time throughout when they never do
+  const uintptr_t pa = reinterpret_cast<uintptr_t>(a), ph = reinterpret_cast<uintptr_t>(hi),
+                  pl = reinterpret_cast<uintptr_t>(lo);
+  long long head = n;
+  for (long long k = 0; k < 4 && k < n; ++k)
+    if ((pa + 8 * k) % 16 == 0 && (ph + 4 * k) % 16 == 0 && (!lo || (pl + 4 * k) % 16 == 0)) {
+      head = k;
+      break;
+    }
+  const long long blocks = std::min<long long>((n / 4 + 255) / 256 + 1, 152LL * 16);
+  df_split_kernel<<<(int)blocks, 256, 0, st>>>(a, hi, lo, n, head);
   return cudaGetLastError();
 }
 

@@ -8,7 +8,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-// hi = fl32(a), lo = fl32(a - hi) for n contiguous values
+// hi = fl32(a), lo = fl32(a - hi) for n contiguous values (lo may be null: hi only)
 cudaError_t launch_df_split(const double* a, float* hi, float* lo, long long n, cudaStream_t st);
 
 // The same for an m x nc column block (ld lda) into ld ldo, each column scaled

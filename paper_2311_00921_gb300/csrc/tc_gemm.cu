@@ -7,22 +7,22 @@
 // MMA (8 rows x 16 bytes per core matrix; K-adjacent core matrices 128 B apart,
 // 8-row groups one K-row of core matrices apart), converted to the MMA input
 // type and, in the x3 modes, split into hi + lo parts (hi·hi + hi·lo + lo·hi
-// is accumulated).  The GEMM kernel (one CTA of 4 warps per 128 x 128 output
-// tile, FP32 accumulator in tensor memory) streams the slabs through a ring of
-// shared-memory stages with cp.async.bulk (the TMA engine, completion counted
-// in bytes on each stage's "full" mbarrier); one thread issues the copies and
-// the tcgen05.mma instructions, whose tcgen05.commit arrives on the stage's
-// "empty" mbarrier that gates its refill.  The refill of a stage waits for the
-// MMAs of the previous slab, so one slab of MMAs is always queued behind the
-// ones executing.  The epilogue reads the tile with tcgen05.ld (each warp its
-// 32 TMEM lanes) and writes alpha·acc + beta·C_in, optionally only on and below
-// the diagonal.
+// is accumulated).  The GEMM kernel is persistent (one CTA per SM, 6 warps,
+// looping over the 128 x 128 output tiles of every node): a producer warp
+// streams the slabs through a ring of shared-memory stages with cp.async.bulk
+// (the TMA engine, completion counted in bytes on each stage's "full"
+// mbarrier); an MMA warp issues tcgen05.mma into one of two FP32 accumulators
+// in tensor memory, commits each stage to its "empty" mbarrier (which gates its
+// refill) and each finished tile to the epilogue; four epilogue warps read the
+// tile with tcgen05.ld (each its 32 TMEM lanes) and write alpha·acc +
+// beta·C_in, optionally only on and below the diagonal, while the next tile's
+// MMAs run into the other accumulator.
 //
-// Every wait is bounded.  The ring's waits poll at most `wait_limit` times (set
-// by the caller; 0 polls = give up at once): on expiry the kernel records
+// Every wait is bounded.  The pipeline's waits poll at most `wait_limit` times
+// (set by the caller; 0 polls = give up at once): on expiry the kernel records
 // HSS_ERR_TIMEOUT in the status word, stops issuing, waits with the long
 // default for the copies and MMAs it has issued, frees its tensor memory and
-// returns without writing the tile.
+// returns without writing the remaining tiles.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -34,7 +34,6 @@
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 32;   // CTA tile and K slab (elements)
-constexpr int TC_THREADS = 128;
 constexpr uint32_t kTmemCols = 128;
 constexpr long long kWaitLimit = 1LL << 24;   // default polls before a wait gives up
 constexpr int kSmemBudget = 200 * 1024;       // dynamic shared memory of the ring
@@ -173,193 +172,275 @@ tc_pack_kernel(const float* __restrict__ s1, int ld1, long long ss1, const float
 
 namespace {
 
-// C (M x N) tile (tm, tn) of node blockIdx.y = Σ over nk K slabs of A_slab · B_slabᵀ
-// (packed operands, see tc_pack_kernel; A has tiles_m row blocks, B the N ones).
+// Persistent, warp-specialised GEMM over a list of output tiles: item it of
+// the list is tile (it % tiles) of node (it / tiles); CTA x takes items x,
+// x + gridDim.x, ...  Warp 0 (one lane) streams the A and B slabs of each item
+// into the ring (cp.async.bulk, bytes counted on the stage's "full" barrier;
+// a stage is refilled once the MMAs that read it have committed to its "empty"
+// barrier).  Warp 1 (one lane) issues the MMAs of item i into tensor-memory
+// accumulator i & 1 (two of TN columns each) and commits the item to "accf";
+// warps 2..5 (lane quarter warp & 3 of tensor memory each) read the
+// accumulator, release it on "acce" and write alpha·acc + beta·C_in, while the
+// MMAs of item i + 1 run into the other accumulator.
+//
+// Every wait polls at most wait_limit times.  A role whose wait expires records
+// HSS_ERR_TIMEOUT and raises the CTA's abort flag; every role leaves its loop
+// at its next wait.  Before the CTA exits, the copies it issued have landed
+// (the producer waits for the stages the MMA warp did not consume) and the MMAs
+// it issued have completed (a final commit waited on with the long default),
+// and then its tensor memory is freed.
+constexpr int TC_WARPS = 6;
+
 template <typename E, int NPASS>
-__global__ void __launch_bounds__(TC_THREADS)
+__global__ void __launch_bounds__(TC_WARPS * 32)
 tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long long sAp,
                const unsigned char* __restrict__ Bp, long long sBp, float alpha, float beta,
                const float* Cin, int ldcin, long long sCin, float* C, int ldc, long long sC,
-               int lower_only, int tiles_m, int stages, int* status, long long wait_limit) {
+               int lower_only, int tiles_m, int tiles, long long items, int stages, int* status,
+               long long wait_limit) {
   constexpr int NPARTS = (NPASS == 3) ? 2 : 1;
   constexpr uint32_t SLAB = slab_bytes<E>();
   constexpr uint32_t OPER = NPARTS * SLAB;    // one operand's slab(s) of a stage
   constexpr uint32_t STAGE = 2 * OPER;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[8], empty[8], done;
+  __shared__ __align__(8) uint64_t full[8], empty[8], accf[2], acce[2], done;
   __shared__ uint32_t tmem_base_s;
-  __shared__ int abort_s;
+  __shared__ volatile int abort_s;
+  __shared__ long long consumed_s;   // slabs whose "full" wait the MMA warp passed
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const long long bz = blockIdx.y;
-  int tm, tn;
-  if (lower_only) {   // tile pairs tm >= tn
-    int t = blockIdx.x, ti = 0;
-    while (t > ti) {
-      t -= ti + 1;
-      ++ti;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // item -> (node, tm, tn)
+  auto item_tile = [&](long long it, long long* node, int* tm, int* tn) {
+    *node = it / tiles;
+    const int t0 = (int)(it % tiles);
+    if (lower_only) {   // tile pairs tm >= tn
+      int t = t0, ti = 0;
+      while (t > ti) {
+        t -= ti + 1;
+        ++ti;
+      }
+      *tm = ti;
+      *tn = t;
+    } else {
+      *tm = t0 % tiles_m;
+      *tn = t0 / tiles_m;
     }
-    tm = ti;
-    tn = t;
-  } else {
-    tm = blockIdx.x % tiles_m;
-    tn = blockIdx.x / tiles_m;
-  }
-  const int m0 = tm * TM, n0 = tn * TN;
-  const unsigned char* a_src = Ap + bz * sAp + (size_t)tm * nk * OPER;
-  const unsigned char* b_src = Bp + bz * sBp + (size_t)tn * nk * OPER;
+  };
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_s)),
-                 "r"(kTmemCols)
+                 "r"(2 * kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < stages; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+    for (int q = 0; q < stages; ++q) {
+      mbar_init(smem_u32(&full[q]), 1);
+      mbar_init(smem_u32(&empty[q]), 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&accf[q]), 1);
+      mbar_init(smem_u32(&acce[q]), 4);   // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
+    consumed_s = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_s;
+  const uint32_t sbase = smem_u32(smem);
+  long long issued = 0;   // producer: slabs whose copies were issued
 
-  if (tid == 0) {
-    const uint32_t sbase = smem_u32(smem);
-    auto load = [&](int kc) {   // slab kc into stage kc % stages
-      const int s = kc % stages;
-      const uint32_t dst = sbase + s * STAGE, fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, STAGE);
-      bulk_g2s(dst, a_src + (size_t)kc * OPER, OPER, fb);
-      bulk_g2s(dst + OPER, b_src + (size_t)kc * OPER, OPER, fb);
-    };
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------------- producer
+    long long g = 0;
+    for (long long it = blockIdx.x; it < items && !abort_s; it += gridDim.x) {
+      long long node;
+      int tm, tn;
+      item_tile(it, &node, &tm, &tn);
+      const unsigned char* a_src = Ap + node * sAp + (size_t)tm * nk * OPER;
+      const unsigned char* b_src = Bp + node * sBp + (size_t)tn * nk * OPER;
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int q = (int)(g % stages);
+        const long long use = g / stages;
+        if (use > 0 && !mbar_wait(smem_u32(&empty[q]), (uint32_t)((use - 1) & 1), wait_limit)) {
+          report_failure(status, -6 /*TIMEOUT*/, -1, (int)blockIdx.x, 1);
+          abort_s = 1;
+          break;
+        }
+        if (abort_s) break;
+        const uint32_t dst = sbase + q * STAGE, fb = smem_u32(&full[q]);
+        mbar_expect_tx(fb, STAGE);
+        bulk_g2s(dst, a_src + (size_t)kc * OPER, OPER, fb);
+        bulk_g2s(dst + OPER, b_src + (size_t)kc * OPER, OPER, fb);
+        issued = g + 1;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issue
     const uint32_t idesc = make_idesc(TcType<E>::fmt, TM, TN);
     constexpr int kpi = TcType<E>::kpi;
     constexpr uint32_t step = (uint32_t)(kpi * sizeof(E) / 16) * 128u;   // bytes per MMA K-step
     constexpr uint32_t sbo = (uint32_t)(TK * sizeof(E) / 16) * 128u;     // 8-row group pitch
-    int loaded = 0;   // slabs whose copies have been issued
-    for (; loaded < nk && loaded < stages; ++loaded) load(loaded);
-    int waited = 0;   // slabs whose copies have landed (full waits passed)
-    int abort = 0;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % stages;
-      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((kc / stages) & 1), wait_limit)) {
-        abort = 1;
+    long long g = 0, i = 0;
+    for (long long it = blockIdx.x; it < items && !abort_s; it += gridDim.x, ++i) {
+      const int a = (int)(i & 1);
+      if (i >= 2 && !mbar_wait(smem_u32(&acce[a]), (uint32_t)(((i >> 1) - 1) & 1), wait_limit)) {
+        report_failure(status, -6 /*TIMEOUT*/, -1, (int)blockIdx.x, 2);
+        abort_s = 1;
         break;
       }
-      waited = kc + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = sbase + s * STAGE, b_hi = a_hi + OPER;
-      const uint32_t a_lo = a_hi + SLAB, b_lo = b_hi + SLAB;
-#pragma unroll
-      for (int ks = 0; ks < TK / kpi; ++ks) {
-        const uint32_t o = ks * step;
-        const uint32_t pa[3] = {a_hi, a_hi, a_lo};
-        const uint32_t pb[3] = {b_hi, b_lo, b_hi};
-#pragma unroll
-        for (int p = 0; p < NPASS; ++p) {
-          const uint64_t ad = make_desc(pa[p] + o, 128, sbo);
-          const uint64_t bd = make_desc(pb[p] + o, 128, sbo);
-          const uint32_t acc = (kc > 0 || ks > 0 || p > 0) ? 1u : 0u;
-          if (TcType<E>::fmt == 2)
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
-          else
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
-        }
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&empty[s]))
-          : "memory");
-      // refill the stage of the previous slab once its MMAs are done
-      if (kc >= 1 && loaded < nk) {
-        const int sp = (kc - 1) % stages;
-        if (!mbar_wait(smem_u32(&empty[sp]), (uint32_t)(((kc - 1) / stages) & 1), wait_limit)) {
-          abort = 1;
+      const uint32_t acc_addr = tmem + (uint32_t)(a * kTmemCols);
+      bool ok = true;
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int q = (int)(g % stages);
+        if (!mbar_wait(smem_u32(&full[q]), (uint32_t)((g / stages) & 1), wait_limit) ||
+            abort_s) {
+          if (!abort_s) report_failure(status, -6 /*TIMEOUT*/, -1, (int)blockIdx.x, 3);
+          abort_s = 1;
+          ok = false;
           break;
         }
-        load(loaded++);
+        consumed_s = g + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_hi = sbase + q * STAGE, b_hi = a_hi + OPER;
+        const uint32_t a_lo = a_hi + SLAB, b_lo = b_hi + SLAB;
+#pragma unroll
+        for (int ks = 0; ks < TK / kpi; ++ks) {
+          const uint32_t o = ks * step;
+          const uint32_t pa[3] = {a_hi, a_hi, a_lo};
+          const uint32_t pb[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
+          for (int p = 0; p < NPASS; ++p) {
+            const uint64_t ad = make_desc(pa[p] + o, 128, sbo);
+            const uint64_t bd = make_desc(pb[p] + o, 128, sbo);
+            const uint32_t acc = (kc > 0 || ks > 0 || p > 0) ? 1u : 0u;
+            if (TcType<E>::fmt == 2)
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_addr),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                  : "memory");
+            else
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_addr),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                  : "memory");
+          }
+        }
+        // the stage is free once these MMAs have read it
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&empty[q]))
+            : "memory");
+      }
+      if (!ok) break;
+      // the accumulator is complete once every MMA of the item has finished
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&accf[a]))
+          : "memory");
+    }
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue
+    const int quarter = warp & 3;   // tensor-memory lanes 32 quarter .. 32 quarter + 31
+    long long i = 0;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x, ++i) {
+      const int a = (int)(i & 1);
+      int got = 1;
+      if (lane == 0) got = mbar_wait(smem_u32(&accf[a]), (uint32_t)((i >> 1) & 1), wait_limit) &&
+                           !abort_s;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      __syncwarp();
+      if (!got) {
+        if (lane == 0 && !abort_s) {
+          report_failure(status, -6 /*TIMEOUT*/, -1, (int)blockIdx.x, 4);
+          abort_s = 1;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      long long node;
+      int tm, tn;
+      item_tile(it, &node, &tm, &tn);
+      const int row = tm * TM + quarter * 32 + lane, n0 = tn * TN;
+      const float* cin = Cin ? Cin + node * sCin : nullptr;
+      float* c = C + node * sC;
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        if (n0 + c0 >= N) break;
+        uint32_t v[32];
+        const uint32_t taddr =
+            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * kTmemCols + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+            "%27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+              "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+              "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c0 + 32 >= TN || n0 + c0 + 32 >= N) {
+          // the last read of this accumulator: hand it back to the MMA warp
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[a]))
+                         : "memory");
+        }
+        if (row < M) {
+          // C_in may be C itself: each element is read and written by this
+          // thread only, so the 32 reads go out together before any write
+          float ci[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            const bool ok = cin && col < N && !(lower_only && col > row);
+            ci[j] = ok ? cin[row + (long long)col * ldcin] : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col >= N || (lower_only && col > row)) continue;
+            float out = alpha * __uint_as_float(v[j]);
+            if (cin) out = fmaf(beta, ci[j], out);
+            c[row + (long long)col * ldc] = out;
+          }
+        }
       }
     }
-    if (abort) {
-      // copies still in flight land before the CTA may exit
-      for (int kc = waited; kc < loaded; ++kc)
-        mbar_wait(smem_u32(&full[kc % stages]), (uint32_t)((kc / stages) & 1), kWaitLimit);
-      abort_s = 1;
-    }
-    // every MMA issued so far completes before `done` arrives
+  }
+  __syncthreads();
+  if (abort_s && warp == 0 && lane == 0) {
+    // copies still in flight land before the CTA may exit
+    for (long long g = consumed_s; g < issued; ++g)
+      mbar_wait(smem_u32(&full[g % stages]), (uint32_t)((g / stages) & 1), kWaitLimit);
+  }
+  if (warp == 1 && lane == 0) {
+    // every MMA issued so far completes before the tensor memory is freed
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&done))
         : "memory");
-    if (!mbar_wait(smem_u32(&done), 0u, kWaitLimit)) abort_s = 2;
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (abort_s) {
-    if (tid == 0) report_failure(status, -6 /*TIMEOUT*/, -1, (int)blockIdx.x, abort_s);
-  } else {
-    // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (tile rows), 32 columns at a time
-    const int row = m0 + warp * 32 + (tid & 31);
-    const float* cin = Cin ? Cin + bz * sCin : nullptr;
-    float* c = C + bz * sC;
-    for (int c0 = 0; c0 < TN; c0 += 32) {
-      if (n0 + c0 >= N) break;
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-          "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-          "%28, %29, %30, %31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-            "=r"(v[31])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        // C_in may be C itself: each element is read and written by this thread
-        // only, so the 32 reads go out together before any write
-        float ci[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          const bool ok = cin && col < N && !(lower_only && col > row);
-          ci[j] = ok ? cin[row + (long long)col * ldcin] : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (col >= N || (lower_only && col > row)) continue;
-          float out = alpha * __uint_as_float(v[j]);
-          if (cin) out = fmaf(beta, ci[j], out);
-          c[row + (long long)col * ldc] = out;
-        }
-      }
-    }
+    if (!mbar_wait(smem_u32(&done), 0u, kWaitLimit))
+      report_failure(status, -6 /*TIMEOUT*/, -1, (int)blockIdx.x, 5);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols)
+                 "r"(2 * kTmemCols)
                  : "memory");
 }
 
@@ -402,18 +483,36 @@ cudaError_t run(int M, int N, int K, const TcOperand& a, const TcOperand& b, flo
   const int stages = std::min<int>(8, kSmemBudget / STAGE);
   const size_t smem = (size_t)stages * STAGE;
   static size_t attr = 0;
+  static int sms = 0, per_sm = 0;
   if (smem > attr) {
     if (cudaFuncSetAttribute(tc_gemm_kernel<E, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return cudaErrorInvalidConfiguration;
     attr = smem;
+    per_sm = 0;
+  }
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorInvalidConfiguration;
+  }
+  if (!per_sm) {
+    // resident CTAs per SM: shared memory, and tensor memory (512 columns an SM)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_gemm_kernel<E, NPASS>,
+                                                      TC_WARPS * 32, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    per_sm = std::min<int>(per_sm, 512 / (2 * (int)kTmemCols));
   }
   const int nk = (K + TK - 1) / TK;
   const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
   const int tiles = lower ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
-  tc_gemm_kernel<E, NPASS><<<dim3(tiles, batch), TC_THREADS, smem, st>>>(
+  const long long items = (long long)tiles * batch;
+  const int grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+  tc_gemm_kernel<E, NPASS><<<grid, TC_WARPS * 32, smem, st>>>(
       M, N, nk, Ap, (long long)(pa / batch), Bp, (long long)(pb / batch), alpha, beta, Cin, ldcin,
-      sCin, C, ldc, sC, lower ? 1 : 0, tiles_m, stages, status, wait_limit);
+      sCin, C, ldc, sC, lower ? 1 : 0, tiles_m, tiles, items, stages, status, wait_limit);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("ir_max_it", ctypes.c_int32),
                 ("ir_tol", ctypes.c_double), ("residual", ctypes.c_int32),
                 ("basis", ctypes.c_int32), ("wait_budget", ctypes.c_int64),
-                ("schedule", ctypes.c_int32), ("ql_panel", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("ql_panel", ctypes.c_int32),
+                ("ir_lanes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 RESIDUALS = {"fp64": 0, "pair32": 1}
@@ -48,8 +49,9 @@ class Tuning(ctypes.Structure):
                 ("factor_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("factor_ms_by_basis", ctypes.c_double * 2),
                 ("solve_ms_by_config", (ctypes.c_double * 2) * 2),
-                ("ql_panel", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("factor_ms_by_panel", ctypes.c_double * 2)]
+                ("ql_panel", ctypes.c_int32), ("ir_lanes", ctypes.c_int32),
+                ("factor_ms_by_panel", ctypes.c_double * 2),
+                ("solve_ms_by_lanes", ctypes.c_double * 2)]
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -230,7 +232,7 @@ class HSS:
 
     def factorize(self, precision="fp64", ir_tol=1e-12, ir_max_it=30, residual="fp64",
                   stream=None, wait_budget=0, basis="householder", schedule="async",
-                  ql_panel=0):
+                  ql_panel=0, ir_lanes=0):
         """residual: arithmetic of the refinement residual of the mixed modes,
         "fp64" or "pair32" (pairs of FP32 numbers, 48-bit significands).
         wait_budget: polls of a device-side pipeline wait (0 = default, < 0 =
@@ -238,9 +240,12 @@ class HSS:
         Householder reconstruction; the method of the basis completion), or
         "auto" (the tuner's).  schedule: "async" (upper solve levels as one launch
         per direction), "levels" or "auto".  ql_panel: 16 or 32 columns per
-        register panel of the Householder kernel in FP32 (0 = default)."""
+        register panel of the Householder kernel in FP32 (0 = default).
+        ir_lanes: refinement lanes of a mixed solve, 1 or 2 (0 = the tuner's
+        choice under schedule="auto", else 1)."""
         opt = Options(PRECISIONS[precision], ir_max_it, ir_tol, RESIDUALS[residual],
-                      BASIS_METHODS[basis], wait_budget, SCHEDULES[schedule], ql_panel)
+                      BASIS_METHODS[basis], wait_budget, SCHEDULES[schedule], ql_panel,
+                      ir_lanes, 0)
         _check(load().hss_factorize(self._h, ctypes.byref(opt), _stream_ptr(stream)),
                "hss_factorize")
         self.precision = precision
@@ -305,7 +310,7 @@ class HSS:
         names_b = {v: k for k, v in BASIS_METHODS.items()}
         names_s = {v: k for k, v in SCHEDULES.items()}
         return {"basis": names_b[t.basis], "ql_panel": t.ql_panel,
-                "schedule": names_s[t.schedule],
+                "schedule": names_s[t.schedule], "ir_lanes": t.ir_lanes,
                 "staging": "fewest_waves" if t.staging else "largest_panels",
                 "from_cache": bool(t.from_cache), "factor_ms": t.factor_ms,
                 "solve_ms": t.solve_ms,
@@ -315,6 +320,8 @@ class HSS:
                     "factor_ms_householder_panel": {
                         f"{16 << k}": t.factor_ms_by_panel[k] for k in range(2)
                         if t.factor_ms_by_panel[k] > 0},
+                    "solve_ms_by_lanes": {f"{k + 1}": t.solve_ms_by_lanes[k] for k in range(2)
+                                          if t.solve_ms_by_lanes[k] > 0},
                     "solve_ms": {f"{names_s[s]}/{'fewest_waves' if g else 'largest_panels'}":
                                  t.solve_ms_by_config[s][g] for s in range(2) for g in range(2)
                                  if t.solve_ms_by_config[s][g] > 0}}}

@@ -301,7 +301,7 @@ def test_refinement_two_lanes_and_one_lane_agree():
     one-column solves (one lane) to the tolerance."""
     h = I.random_hss(4, 64, 16, seed=21, orthonormal=False)
     dev = hss.HSS(h)
-    dev.factorize("fp32", ir_tol=1e-13)
+    dev.factorize("fp32", ir_tol=1e-13, ir_lanes=2)
     b = I.rhs(h.n, 16, 8)
     b[:, 9:] *= 1e6                     # the second lane's columns at another scale
     x2 = dev.solve(hss.colmajor(b)).cpu().numpy()
@@ -556,6 +556,8 @@ def test_autotuner_choices_and_cache(prec, tmp_path):
     panels = t["measured"]["factor_ms_householder_panel"]
     assert set(panels) == ({"16"} if prec == "fp64" else {"16", "32"}), t
     assert t["ql_panel"] in (16, 32) and min(t["measured"]["factor_ms"].values()) == t["factor_ms"]
+    assert t["ir_lanes"] == 1 or prec == "fp32"
+    assert set(t["measured"]["solve_ms_by_lanes"]) == ({"1"} if prec == "fp64" else {"1", "2"})
     b = I.rhs(h.n, 4, 1)
     x = dev.solve(hss.colmajor(b)).cpu().numpy()
     x_ref = O.solve(O.factor(h), b)
