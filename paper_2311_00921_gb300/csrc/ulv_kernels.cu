@@ -650,6 +650,26 @@ HSS_DEVINL void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// 8 consecutive values from 16-byte aligned shared memory, in 128-bit loads
+HSS_DEVINL void load8(const float* p, float (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float4 f = reinterpret_cast<const float4*>(p)[q];
+    v[4 * q] = f.x;
+    v[4 * q + 1] = f.y;
+    v[4 * q + 2] = f.z;
+    v[4 * q + 3] = f.w;
+  }
+}
+HSS_DEVINL void load8(const double* p, double (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 f = reinterpret_cast<const double2*>(p)[q];
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+
 // 16 consecutive values from 16-byte aligned shared memory, in 128-bit loads
 HSS_DEVINL void load16(const float* p, float (&v)[16]) {
 #pragma unroll
@@ -804,6 +824,86 @@ HSS_DEVINL void q_apply(T* y, T* yr, bool fill, int b, int nrhs, const T* V, con
   }
 }
 
+// The same Q application with all of V resident in shared memory (Vs, b x r,
+// pitch Pv odd, staged by the caller; T read through L1): no slab staging and
+// no barriers inside a phase.  Phase (0) t1 = Vᵀ y and (1) t2 = op(T) t1 give
+// each thread one row of t1 / t2 and 8 of the 16 right-hand sides (two
+// threads a row); phase (2) y -= V t2 gives each thread rows of y.  Called by
+// every thread with yr (and y when fill) visible and the staging of Vs
+// committed; returns with yr (or y) updated and visible.
+constexpr int kVres = 4;   // flag in the NBUF argument: V resident in shared memory
+
+template <typename T>
+HSS_DEVINL void q_apply_res(T* y, T* yr, bool fill, int b, int nrhs, const T* Vs, int Pv,
+                            const T* Tm, int r, bool transpose, T* t1, T* t2) {
+  const int tid = threadIdx.x;
+  if (fill) {
+    for (int e = tid; e < b * 16; e += NT) {
+      const int i = e / 16, j = e % 16;
+      yr[e] = j < nrhs ? y[i + j * b] : T(0);
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  const int j0 = (tid & 1) * 8;
+  // (0) t1 row q = Σ_i V(i, q) yr row i
+  for (int q = tid >> 1; q < r; q += NT / 2) {
+    T a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = T(0);
+    const T* vq = Vs + (size_t)q * Pv;
+    for (int i = 0; i < b; ++i) {
+      const T v = vq[i];
+      T yv[8];
+      load8(yr + i * 16 + j0, yv);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = fma(v, yv[j], a[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t1[q * 16 + j0 + j] = a[j];
+  }
+  __syncthreads();
+  // (1) t2 row p = Σ_q op(T)(p, q) t1 row q; op(T) = Tᵀ (forward) reads
+  // column p of T, T (backward) row p
+  for (int p = tid >> 1; p < r; p += NT / 2) {
+    T a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = T(0);
+    for (int q = 0; q < r; ++q) {
+      const T tv = transpose ? __ldg(Tm + q + (size_t)p * r) : __ldg(Tm + p + (size_t)q * r);
+      T tq[8];
+      load8(t1 + q * 16 + j0, tq);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = fma(tv, tq[j], a[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t2[p * 16 + j0 + j] = a[j];
+  }
+  __syncthreads();
+  // (2) y row i -= Σ_q V(i, q) t2 row q
+  for (int i = tid; i < b; i += NT) {
+    T a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = T(0);
+    for (int q = 0; q < r; ++q) {
+      const T v = Vs[i + (size_t)q * Pv];
+      T tv[16];
+      load16(t2 + q * 16, tv);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) a[j] = fma(v, tv[j], a[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < nrhs) {
+        if (y)
+          y[i + j * b] -= a[j];
+        else
+          yr[i * 16 + j] -= a[j];
+      }
+  }
+  __syncthreads();
+}
+
 // a load of a vector that another CTA of the same kernel may have written:
 // through L2 (CG) so that no stale L1 line is read
 template <bool CG, typename T>
@@ -823,6 +923,8 @@ HSS_DEVINL void fwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
   __shared__ __align__(16) T zt[NB * 16];
   T* y = reinterpret_cast<T*>(smem_raw);   // b x nrhs, ld = b
   const int P = b | 1;
+  const bool vres = (NBUF & kVres) && Vb;   // V resident in the panel region
+  NBUF &= ~kVres;
   // Q application (Vb given): y row by row, partial sums, t1 and t2 (r x 16)
   const size_t qsz = Vb ? (size_t)b * 16 + (size_t)NT * ZP + (size_t)32 * r : 0;
   T* yr = y + (((size_t)b * nrhs + 15) & ~size_t(15));
@@ -835,14 +937,18 @@ HSS_DEVINL void fwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
   const int nblk = (c + CB - 1) / CB;
   if (!Vb && nblk > 0) stage_panel(M, ldm, 0, min(CB, c), b, Lbuf, P);
+  if (vres) stage_block(Vb + (long long)node * sV, b, 0, b, 0, r, Lbuf, P);
   for (int e = tid; e < b * nrhs; e += NT) {
     const int i = e % b, j = e / b;
     y[i + j * b] = ldv<CG>(x + i + (long long)j * ldx);
   }
   if (Vb) {   // y := Qᵀ y, then the first panel
     __syncthreads();
-    q_apply(y, yr, true, b, nrhs, Vb + (long long)node * sV, Tb + (long long)node * sT, r, true,
-            Lbuf, P, CB, NBUF, zpq, t1, t2);
+    if (vres)
+      q_apply_res(y, yr, true, b, nrhs, Lbuf, P, Tb + (long long)node * sT, r, true, t1, t2);
+    else
+      q_apply(y, yr, true, b, nrhs, Vb + (long long)node * sV, Tb + (long long)node * sT, r, true,
+              Lbuf, P, CB, NBUF, zpq, t1, t2);
     if (nblk > 0) stage_panel(M, ldm, 0, min(CB, c), b, Lbuf, P);
   }
   for (int bi = 0; bi < nblk; ++bi) {
@@ -948,6 +1054,8 @@ HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
   T* t2 = t1 + (size_t)16 * (Vb ? r : 0);
   T* Lbuf = t2 + (size_t)16 * (Vb ? r : 0);
   const int P = b | 1;
+  const bool vres = (NBUF & kVres) && Vb;   // V resident in the panel region for Q
+  NBUF &= ~kVres;
   const T* M = Mb + (long long)node * sM;
   T* x = X + (long long)node * sX;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
@@ -1036,8 +1144,14 @@ HSS_DEVINL void bwd_node(int node, const T* __restrict__ Mb, int ldm, long long 
   cp_async_wait<0>();
   if (Vb) {   // x := Q x, on the row-major vector
     __syncthreads();
-    q_apply<T>(nullptr, xt, false, b, nrhs, Vb + (long long)node * sV, Tb + (long long)node * sT,
-               r, false, Lbuf, P, CB, NBUF, zp, t1, t2);
+    if (vres) {
+      stage_block(Vb + (long long)node * sV, b, 0, b, 0, r, Lbuf, P);
+      q_apply_res<T>(nullptr, xt, false, b, nrhs, Lbuf, P, Tb + (long long)node * sT, r, false,
+                     t1, t2);
+    } else {
+      q_apply<T>(nullptr, xt, false, b, nrhs, Vb + (long long)node * sV,
+                 Tb + (long long)node * sT, r, false, Lbuf, P, CB, NBUF, zp, t1, t2);
+    }
   }
   __syncthreads();
   for (int e = tid; e < b * nrhs; e += NT) {
@@ -1284,13 +1398,16 @@ cudaError_t launch_scatter_ss(const T* M, int ldm, long long sM, int c, int r, T
 // shared memory of a sweep: the node vector, the Q application's two r x 16
 // buffers, and NBUF staged panels of P x CB
 template <typename T>
-size_t trsv_smem(int b, int nrhs, int r, int CB, int NBUF, bool bwd) {
+size_t trsv_smem(int b, int nrhs, int r, int CB, int NBUF, bool bwd, bool vres = false) {
   // forward: the column-major vector (padded to 16 elements), plus its row-major
   // copy and the partial sums when Q is applied; backward: the row-major vector
-  // and the partial sums only
+  // and the partial sums only.  The panel region also holds all of V (pitch
+  // b | 1) when V is resident.
   const size_t vec = bwd ? 0 : ((size_t)b * nrhs + 15) & ~size_t(15);
   const size_t rowmajor = (bwd || r > 0) ? (size_t)b * 16 + (size_t)NT * ZP : 0;
-  return (vec + rowmajor + (size_t)32 * r + (size_t)NBUF * (b | 1) * CB) * sizeof(T);
+  size_t region = (size_t)NBUF * (b | 1) * CB;
+  if (vres) region = std::max(region, (size_t)r * (b | 1));
+  return (vec + rowmajor + (size_t)32 * r + region) * sizeof(T);
 }
 
 // Panel staging of a sweep launch of `nodes` CTAs.  staging = 0: the largest
@@ -1309,6 +1426,27 @@ cudaError_t trsv_config(K kernel, int b, int nrhs, int r, bool bwd, int* CB, int
       sms = 1;
   }
   long long best_waves = -1;
+  // with Q fused (r > 0): first the layouts that keep all of V resident
+  for (int q = 0; r > 0 && q < 5; ++q) {
+    const size_t s = trsv_smem<T>(b, nrhs, r, cbs[q], bufs[q], bwd, true);
+    if (!smem_opt_in(kernel, s)) continue;
+    long long waves = 0;
+    if (staging == 1) {
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, NT, s) != cudaSuccess ||
+          occ < 1)
+        occ = 1;
+      waves = (nodes + (long long)sms * occ - 1) / ((long long)sms * occ);
+    }
+    if (best_waves < 0 || waves < best_waves) {
+      best_waves = waves;
+      *CB = cbs[q];
+      *NBUF = bufs[q] | kVres;
+      *sm = s;
+    }
+    if (staging == 0) break;
+  }
+  if (best_waves >= 0) return cudaSuccess;
   for (int q = 0; q < 5; ++q) {
     const size_t s = trsv_smem<T>(b, nrhs, r, cbs[q], bufs[q], bwd);
     if (!smem_opt_in(kernel, s)) continue;
