@@ -462,6 +462,15 @@ def run_ours(args):
     resid = args.residual if prec != "fp64" else "fp64"
     tune_cache = os.environ.get("HSS_TUNE_CACHE") or os.path.join(
         tempfile.gettempdir(), f"hss_tune_{os.getpid()}.txt")
+    choice = None
+    if prec == "auto":
+        # the mixed arithmetic of the factor is a tuned choice too: the tuner's
+        # factor + solve time of each (all refine to the same 1e-12 with the
+        # same residual)
+        cand = {p: dev.tune(p, w.nrhs, resid, cache=tune_cache) for p in ("fp32", "tf32", "bf16")}
+        prec = min(cand, key=lambda p: cand[p]["factor_ms"] + cand[p]["solve_ms"])
+        choice = {"chosen": prec, "tuned_factor_plus_solve_ms": {
+            p: t["factor_ms"] + t["solve_ms"] for p, t in cand.items()}}
     tuning = {prec: dev.tune(prec, w.nrhs, resid, cache=tune_cache)}
     for _ in range(args.warmup):
         dev.factorize(prec, residual=resid, basis="auto", schedule=args.schedule)
@@ -577,7 +586,8 @@ def run_ours(args):
                "roofline": roofline_of(ser["trace"], peaks, nser, prec,
                                        overlapped=head["trace"], overlapped_steps=args.steps),
                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
-               "autotune": tuning, "gpu_launches": head["launches"]}
+               "autotune": tuning, "precision_choice": choice,
+               "gpu_launches": head["launches"]}
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -833,7 +843,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "tf32", "bf16", "fp32"],
+    ap.add_argument("--precision", default="auto",
+                    choices=["auto", "fp64", "tf32", "bf16", "fp32"],
                     help="factor arithmetic; non-fp64 modes refine in FP64 to 1e-12")
     ap.add_argument("--residual", default="fp64", choices=["fp64", "pair32"],
                     help="arithmetic of the refinement residual of the mixed modes")
