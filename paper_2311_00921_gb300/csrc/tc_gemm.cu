@@ -179,9 +179,11 @@ namespace {
 // a stage is refilled once the MMAs that read it have committed to its "empty"
 // barrier).  Warp 1 (one lane) issues the MMAs of item i into tensor-memory
 // accumulator i & 1 (two of TN columns each) and commits the item to "accf";
-// warps 2..5 (lane quarter warp & 3 of tensor memory each) read the
-// accumulator, release it on "acce" and write alpha·acc + beta·C_in, while the
-// MMAs of item i + 1 run into the other accumulator.
+// warps 2..9 (lane quarter warp & 3 of tensor memory, and one half of the
+// tile's columns, each) read the accumulator, release it on "acce" and write
+// alpha·acc + beta·C_in, while the MMAs of item i + 1 run into the other
+// accumulator.  Eight epilogue warps keep twice the global loads and stores in
+// flight of four, so the epilogue of a tile is not longer than its MMAs.
 //
 // Every wait polls at most wait_limit times.  A role whose wait expires records
 // HSS_ERR_TIMEOUT and raises the CTA's abort flag; every role leaves its loop
@@ -189,7 +191,7 @@ namespace {
 // (the producer waits for the stages the MMA warp did not consume) and the MMAs
 // it issued have completed (a final commit waited on with the long default),
 // and then its tensor memory is freed.
-constexpr int TC_WARPS = 6;
+constexpr int TC_WARPS = 10;
 
 template <typename E, int NPASS>
 __global__ void __launch_bounds__(TC_WARPS * 32)
@@ -241,7 +243,7 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&accf[q]), 1);
-      mbar_init(smem_u32(&acce[q]), 4);   // one arrival per epilogue warp
+      mbar_init(smem_u32(&acce[q]), TC_WARPS - 2);   // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -350,6 +352,7 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
   } else if (warp >= 2) {
     // ---------------------------------------------------------------- epilogue
     const int quarter = warp & 3;   // tensor-memory lanes 32 quarter .. 32 quarter + 31
+    const int half = (warp - 2) >> 2;   // columns [64 half, 64 half + 64) of the tile
     long long i = 0;
     for (long long it = blockIdx.x; it < items; it += gridDim.x, ++i) {
       const int a = (int)(i & 1);
@@ -372,8 +375,15 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
       const int row = tm * TM + quarter * 32 + lane, n0 = tn * TN;
       const float* cin = Cin ? Cin + node * sCin : nullptr;
       float* c = C + node * sC;
-      for (int c0 = 0; c0 < TN; c0 += 32) {
-        if (n0 + c0 >= N) break;
+      const int cb = half * (TN / 2), ce = min(cb + TN / 2, N - n0);
+      if (ce <= cb) {   // no columns of this half in the tile: release at once
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[a]))
+                       : "memory");
+        continue;
+      }
+      for (int c0 = cb; c0 < ce; c0 += 32) {
         uint32_t v[32];
         const uint32_t taddr =
             tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * kTmemCols + c0);
@@ -390,8 +400,8 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
             : "r"(taddr)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (c0 + 32 >= TN || n0 + c0 + 32 >= N) {
-          // the last read of this accumulator: hand it back to the MMA warp
+        if (c0 + 32 >= ce) {
+          // this warp's last read of the accumulator: hand it back
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0)
