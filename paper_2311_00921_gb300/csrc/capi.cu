@@ -546,9 +546,10 @@ int factor_levels(hss_s* h, Factor<T>& f, T* zq, cudaStream_t st, bool split_d) 
   return HSS_OK;
 }
 
-// Blocked right-looking Cholesky of the FP64 root block (last step of Alg. 2): a
-// one-CTA panel step (diagonal block and the rows below it) and a many-CTA
-// GEMM for the trailing update, so the 2r x 2r root is not bound to one SM.
+// Blocked right-looking Cholesky of the FP64 root block (last step of Alg. 2):
+// per 32-column panel, the diagonal block and the rows below it with the rows
+// split over CTAs of 32 rows, then the trailing update as a batch of 16-column
+// blocks, so that neither step queues on one SM's FP64 pipe.
 int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
   double* slots = h->logdet_part + ((2LL << h->L) - 1);
   if (cudaMemsetAsync(slots, 0, kRootPanels * sizeof(double), st) != cudaSuccess ||
@@ -560,13 +561,21 @@ int root_cholesky(hss_s* h, double* R, int b0, cudaStream_t st) {
     {
       Launch k(h, HSS_K_PCHOL, panel_flops(rows, kb), st);
       HSS_TRY(launch_chol_panel<double>(Mk, b0, 0, rows, kb, slots + p, 0, 0, k0, h->status, 1,
-                                        false, st));
+                                        false, st, std::max(1, (rows - kb + 31) / 32)));
     }
     const int nt = rows - kb;
     if (nt > 0) {
       double* P = Mk + kb;   // rows below the panel
-      gemm<double>(h, false, true, nt, nt, kb, -1.0, P, b0, 0, P, b0, 0, 1.0,
-                   R + (k0 + kb) + (long long)(k0 + kb) * b0, b0, 0, 1, st);
+      double* C = R + (k0 + kb) + (long long)(k0 + kb) * b0;
+      // column block j (16 columns) of the trailing matrix: C_j -= P P_jᵀ, all
+      // blocks in one batched launch; a last partial block on its own
+      const int nb16 = nt / 16, tail = nt - 16 * nb16;
+      if (nb16 > 0)
+        gemm<double>(h, false, true, nt, 16, kb, -1.0, P, b0, 0, P, b0, 16, 1.0, C, b0,
+                     16LL * b0, nb16, st);
+      if (tail > 0)
+        gemm<double>(h, false, true, nt, tail, kb, -1.0, P, b0, 0, P + 16 * nb16, b0, 0, 1.0,
+                     C + 16LL * nb16 * b0, b0, 0, 1, st);
     }
   }
   return check_launch();

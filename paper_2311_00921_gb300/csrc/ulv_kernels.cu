@@ -550,10 +550,14 @@ HSS_DEVINL T reg_select(const T (&a)[NB], int i) {
 
 // ------------------------------------------------------------------ Cholesky panel
 // One panel (kb <= NB columns) of a right-looking blocked Cholesky, one CTA per
-// node; the trailing update is a separate level-wide SYRK.  Warp 0 factors the
-// kb x kb diagonal block in registers (lane i holds row i, the pivot and the
-// column entries travel by shuffles), then every thread solves rows of
-// X L_11ᵀ = M_21 below it in registers against the block kept in shared memory.
+// node (blockIdx.x) and row split (blockIdx.y); the trailing update is a
+// separate level-wide SYRK.  Warp 0 factors the kb x kb diagonal block in
+// registers (lane i holds row i, the pivot and the column entries travel by
+// shuffles), then every thread solves rows of X L_11ᵀ = M_21 below it in
+// registers against the block kept in shared memory.  With several row splits
+// (a lone node, e.g. the root, whose row solves would otherwise queue on one
+// SM's FP64 pipe) each CTA factors the diagonal block itself and solves its own
+// share of the rows; split 0 alone writes the block, the log-det and a failure.
 // The node's log-det slot gets (or, with accumulate, adds) 2 Σ log L_jj.
 template <typename T>
 __global__ void __launch_bounds__(NT)
@@ -563,6 +567,7 @@ chol_panel_kernel(T* Mb, int ldm, long long sM, int rows, int kb, double* logdet
   __shared__ T dinv[NB];
   __shared__ int fail;
   const int node = blockIdx.x;
+  const bool lead = blockIdx.y == 0;
   T* M = Mb + (long long)node * sM;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (wid == 0) {
@@ -589,19 +594,20 @@ chol_panel_kernel(T* Mb, int ldm, long long sM, int rows, int kb, double* logdet
     }
     if (lane == 0) fail = bad >= 0;
     if (bad >= 0) {
-      if (lane == 0) report_failure(status, -3 /*NOT_SPD*/, level, node0 + node, col0 + bad);
+      if (lane == 0 && lead)
+        report_failure(status, -3 /*NOT_SPD*/, level, node0 + node, col0 + bad);
     } else {
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (lane < kb && t <= lane) {
-          M[lane + (long long)t * ldm] = a[t];
+          if (lead) M[lane + (long long)t * ldm] = a[t];
           Ls[lane][t] = a[t];
         }
       const T dg = reg_select(a, lane);
       if (lane < kb) dinv[lane] = T(1) / dg;
       double ld = lane < kb ? log((double)dg) : 0.0;
       ld = warp_sum(ld);
-      if (lane == 0 && logdet_part) {
+      if (lane == 0 && logdet_part && lead) {
         if (accumulate)
           logdet_part[node] += 2.0 * ld;
         else
@@ -611,7 +617,10 @@ chol_panel_kernel(T* Mb, int ldm, long long sM, int rows, int kb, double* logdet
   }
   __syncthreads();
   if (fail) return;
-  for (int i = kb + tid; i < rows; i += NT) {
+  // this split's rows: [kb + per y, kb + per (y + 1))
+  const int per = (rows - kb + gridDim.y - 1) / gridDim.y;
+  const int i0 = kb + per * blockIdx.y, i1 = min(rows, i0 + per);
+  for (int i = i0 + tid; i < i1; i += NT) {
     T x[NB];
 #pragma unroll
     for (int t = 0; t < NB; ++t) x[t] = t < kb ? M[i + (long long)t * ldm] : T(0);
@@ -1359,10 +1368,12 @@ cudaError_t launch_pchol(T* M, int ldm, long long sM, int b, int c, T* PA, int l
 template <typename T>
 cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, double* logdet_part,
                               int level, int node0, int col0, int* status, int nodes,
-                              bool accumulate, cudaStream_t st) {
-  if (kb < 1 || kb > NB || rows < kb) return cudaErrorInvalidValue;
-  chol_panel_kernel<T><<<nodes, NT, 0, st>>>(M, ldm, sM, rows, kb, logdet_part, level, node0, col0,
-                                             status, accumulate ? 1 : 0);
+                              bool accumulate, cudaStream_t st, int splits) {
+  if (kb < 1 || kb > NB || rows < kb || splits < 1 || splits > 65535)
+    return cudaErrorInvalidValue;
+  chol_panel_kernel<T><<<dim3(nodes, splits), NT, 0, st>>>(M, ldm, sM, rows, kb, logdet_part,
+                                                           level, node0, col0, status,
+                                                           accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1588,7 +1599,7 @@ void launch_logdet_reduce(const double* part, int n, double* out, cudaStream_t s
                                          const T*, long long, int, int, cudaStream_t, int);       \
   template size_t ql_smem<T>(int, int, int);                                                     \
   template cudaError_t launch_chol_panel<T>(T*, int, long long, int, int, double*, int, int, int,\
-                                            int*, int, bool, cudaStream_t);                       \
+                                            int*, int, bool, cudaStream_t, int);                  \
   template cudaError_t launch_scatter_ss<T>(const T*, int, long long, int, int, T*, int,           \
                                             long long, int, cudaStream_t);                       \
   template cudaError_t launch_tree_fwd<T>(const TreeLevels<T>&, int, int, int, int, int, int*,    \

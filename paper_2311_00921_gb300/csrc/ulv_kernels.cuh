@@ -64,12 +64,13 @@ size_t ql_smem(int b, int r, int NBP);
 
 // One panel of a blocked Cholesky, for every node of a batch (stride sM): factor
 // the kb x kb diagonal block at the top of each rows x rows matrix M (ld ldm)
-// and solve the rows below it; the trailing update is left to the caller.
-// Writes (or, with accumulate, adds) 2 Σ log diag to logdet_part[node].
+// and solve the rows below it, split over `splits` CTAs a node; the trailing
+// update is left to the caller.  Writes (or, with accumulate, adds)
+// 2 Σ log diag to logdet_part[node].
 template <typename T>
 cudaError_t launch_chol_panel(T* M, int ldm, long long sM, int rows, int kb, double* logdet_part,
                               int level, int node0, int col0, int* status, int nodes,
-                              bool accumulate, cudaStream_t st);
+                              bool accumulate, cudaStream_t st, int splits = 1);
 
 // The merge step of Alg. 2 as its own pass: Â^SS of node i (lower triangle
 // of M[c:, c:], r x r) into block (i & 1) of parent i / 2's diagonal, both triangles.
