@@ -177,8 +177,9 @@ def measured_fp64_peak(torch):
 
 
 def traffic_record(kernel, prec):
-    """DRAM bytes per launch of `kernel` in arithmetic `prec` from the committed
-    ncu summary, or None if the kernel source changed since those counters were
+    """(DRAM bytes per full-size launch, the launch they describe, its
+    algorithmic bytes) of `kernel` in arithmetic `prec` from the committed ncu
+    summary, or None if the kernel source changed since those counters were
     taken."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -195,7 +196,10 @@ def traffic_record(kernel, prec):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if sha != kv.get("src_sha"):
             return None
-        return float(kv["bytes_per_launch"]) * float(kv.get("scale", 1.0))
+        scale = float(kv.get("scale", 1.0))
+        algo = kv.get("algo_bytes_per_launch")
+        return (float(kv["bytes_per_launch"]) * scale, kv.get("case", "").replace("_", " "),
+                float(algo) * scale if algo else None)
     return None
 
 
@@ -374,9 +378,12 @@ def roofline_of(tr, peaks, steps, prec_mode="fp64", overlapped=None, overlapped_
         prec = "pair32"
         peak = peaks["f32"] / PAIR_OPS_PER_FLOP if peaks else None
     total = sum(v[0] for v in tr.values())
+    traffic = traffic_record(kname, prec)
     out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": (achieved / peak) if peak else None,
-           "traffic": traffic_record(kname, prec),
+           "traffic": traffic[0] if traffic else None,
+           "traffic_launch": traffic[1] if traffic else None,
+           "traffic_algorithmic_bytes": traffic[2] if traffic else None,
            "kernel": f"{kname} ({PREC_LABEL.get(prec, prec)})",
            "peak_source": PEAK_SOURCE.get(prec),
            "timing": "serialized pass (basis chain on the main stream), CUDA events per launch",
