@@ -788,10 +788,19 @@ def run_large(args):
         info = dev.last_info()
         res = b - dev.matvec(x)
         rel = (torch.linalg.vector_norm(res, dim=0) / torch.linalg.vector_norm(b, dim=0)).max()
+        # one more step with the launches logged one after the other: where the time goes
+        dev.trace(True, serialize=True)
+        dev.factorize(prec, basis="auto", schedule="auto")
+        dev.solve(b, x)
+        torch.cuda.synchronize()
+        per_class = {k: round(v[0], 3) for k, v in sorted(dev.trace_read().items())}
+        dev.trace(False)
         out[prec] = {"factor_ms": fms, "solve_ms": sms, "ms_per_step": fms + sms,
                      "tflops": fl / ((fms + sms) / 1e3) / 1e12, "ir_iterations": info["ir_iters"],
                      "max_rel_residual_fp64_matvec": rel.item(),
-                     "autotune": {k: tune[k] for k in ("basis", "ql_panel", "schedule", "staging")}}
+                     "autotune": {k: tune[k] for k in ("basis", "ql_panel", "schedule", "staging",
+                                                       "ir_lanes")},
+                     "serialized_ms_by_kernel_class": per_class}
     out["device_memory_gb"] = torch.cuda.max_memory_allocated() / 1e9
     free, total = torch.cuda.mem_get_info()
     out["device_memory_in_use_gb"] = (total - free) / 1e9

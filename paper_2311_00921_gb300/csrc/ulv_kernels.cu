@@ -27,6 +27,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "ulv_kernels.cuh"
@@ -1288,18 +1291,39 @@ __global__ void logdet_reduce_kernel(const double* part, int n, double* out) {
 // opt a kernel into `bytes` of dynamic shared memory (plus its static part);
 // false if the device cannot give that much
 // (the 48 KB default holds static + dynamic shared memory together)
+// The answers are remembered per (device, kernel, bytes): the queries and the
+// attribute change cost microseconds of host time, and the sweeps ask before
+// every launch.
 template <typename K>
 bool smem_opt_in(K kernel, size_t bytes) {
-  cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
-  if (bytes + fa.sharedSizeBytes <= 48 * 1024) return true;
-  int dev = 0, optin = 0;
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, size_t>, bool> memo;
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (bytes + fa.sharedSizeBytes > (size_t)optin) return false;
-  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return true;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-         cudaSuccess;
+  const auto key = std::make_tuple(dev, reinterpret_cast<const void*>(kernel), bytes);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+  }
+  bool ok = false;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (bytes + fa.sharedSizeBytes <= 48 * 1024)
+      ok = true;
+    else if (bytes + fa.sharedSizeBytes <= (size_t)optin)
+      ok = (size_t)fa.maxDynamicSharedSizeBytes >= bytes ||
+           cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes) == cudaSuccess;
+  } else {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  memo[key] = ok;
+  return ok;
 }
 
 template <typename T>
@@ -1426,8 +1450,44 @@ size_t trsv_smem(int b, int nrhs, int r, int CB, int NBUF, bool bwd, bool vres =
 // panels).  staging = 1: the fewest waves of CTAs over the SMs (smaller panels
 // let more CTAs share an SM), ties to the larger staging.
 template <typename T, typename K>
+cudaError_t trsv_config_uncached(K kernel, int b, int nrhs, int r, bool bwd, int* CB, int* NBUF,
+                                 size_t* sm, int nodes, int staging);
+
+// the choice, remembered per (device, kernel, shape, nodes, staging): it queries
+// the occupancy calculator, which costs microseconds of host time per launch
+template <typename T, typename K>
 cudaError_t trsv_config(K kernel, int b, int nrhs, int r, bool bwd, int* CB, int* NBUF,
                         size_t* sm, int nodes = 1, int staging = 0) {
+  struct Choice { cudaError_t e; int cb, nbuf; size_t sm; };
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, int, int, int, int, int>, Choice> memo;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, reinterpret_cast<const void*>(kernel), b, nrhs, r,
+                                   (int)bwd, staging == 1 ? nodes : 0, staging);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    const auto it = memo.find(key);
+    if (it != memo.end()) {
+      *CB = it->second.cb;
+      *NBUF = it->second.nbuf;
+      *sm = it->second.sm;
+      return it->second.e;
+    }
+  }
+  Choice c{cudaSuccess, 0, 0, 0};
+  c.e = trsv_config_uncached<T>(kernel, b, nrhs, r, bwd, &c.cb, &c.nbuf, &c.sm, nodes, staging);
+  std::lock_guard<std::mutex> g(mu);
+  memo[key] = c;
+  *CB = c.cb;
+  *NBUF = c.nbuf;
+  *sm = c.sm;
+  return c.e;
+}
+
+template <typename T, typename K>
+cudaError_t trsv_config_uncached(K kernel, int b, int nrhs, int r, bool bwd, int* CB, int* NBUF,
+                                 size_t* sm, int nodes, int staging) {
   const int cbs[5] = {32, 32, 16, 16, 8}, bufs[5] = {2, 1, 2, 1, 1};
   static int sms = 0;
   if (!sms) {
