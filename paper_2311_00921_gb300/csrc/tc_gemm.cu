@@ -199,7 +199,7 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
                const unsigned char* __restrict__ Bp, long long sBp, float alpha, float beta,
                const float* Cin, int ldcin, long long sCin, float* C, int ldc, long long sC,
                int lower_only, int tiles_m, int tiles, long long items, int stages, int* status,
-               long long wait_limit) {
+               long long wait_limit, int b_krot) {
   constexpr int NPARTS = (NPASS == 3) ? 2 : 1;
   constexpr uint32_t SLAB = slab_bytes<E>();
   constexpr uint32_t OPER = NPARTS * SLAB;    // one operand's slab(s) of a stage
@@ -278,7 +278,10 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
         const uint32_t dst = sbase + q * STAGE, fb = smem_u32(&full[q]);
         mbar_expect_tx(fb, STAGE);
         bulk_g2s(dst, a_src + (size_t)kc * OPER, OPER, fb);
-        bulk_g2s(dst + OPER, b_src + (size_t)kc * OPER, OPER, fb);
+        // b_krot: B is A's packed buffer with its K slabs rotated (the rank-2r
+        // update's right operand [Q P] is the left one [P Q] with halves swapped)
+        const int kb = b_krot ? (kc + b_krot) % nk : kc;
+        bulk_g2s(dst + OPER, b_src + (size_t)kb * OPER, OPER, fb);
         issued = g + 1;
       }
     }
@@ -476,20 +479,24 @@ void pack(const TcOperand& x, int rows, int K, int batch, unsigned char* out, cu
       x.kcontig ? 1 : 0, rows, nkb, out, s_out);
 }
 
+// b_rot_of_a: b is a with its two K halves swapped (K even, each half a whole
+// number of K slabs, M = N): B is read from A's packed buffer, K-rotated.
 template <typename E, int NPASS>
 cudaError_t run(int M, int N, int K, const TcOperand& a, const TcOperand& b, float alpha,
                 float beta, const float* Cin, int ldcin, long long sCin, float* C, int ldc,
                 long long sC, bool lower, int batch, void* ws, size_t ws_bytes, int* status,
-                long long wait_limit, cudaStream_t st) {
+                long long wait_limit, cudaStream_t st, bool b_rot_of_a = false) {
   constexpr int NPARTS = (NPASS == 3) ? 2 : 1;
   constexpr uint32_t STAGE = 2 * NPARTS * slab_bytes<E>();
-  const size_t pa = packed_bytes<E, NPASS>(M, K, batch), pb = packed_bytes<E, NPASS>(N, K, batch);
+  const bool rot = b_rot_of_a && M == N && K % (2 * TK) == 0;
+  const size_t pa = packed_bytes<E, NPASS>(M, K, batch),
+               pb = rot ? 0 : packed_bytes<E, NPASS>(N, K, batch);
   if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
   if (pa + pb > ws_bytes || batch > 65535) return cudaErrorInvalidValue;
   unsigned char* Ap = static_cast<unsigned char*>(ws);
-  unsigned char* Bp = Ap + pa;
+  unsigned char* Bp = rot ? Ap : Ap + pa;
   pack<E, NPASS>(a, M, K, batch, Ap, st);
-  pack<E, NPASS>(b, N, K, batch, Bp, st);
+  if (!rot) pack<E, NPASS>(b, N, K, batch, Bp, st);
   const int stages = std::min<int>(8, kSmemBudget / STAGE);
   const size_t smem = (size_t)stages * STAGE;
   static size_t attr = 0;
@@ -521,8 +528,9 @@ cudaError_t run(int M, int N, int K, const TcOperand& a, const TcOperand& b, flo
   const long long items = (long long)tiles * batch;
   const int grid = (int)std::min<long long>(items, (long long)sms * per_sm);
   tc_gemm_kernel<E, NPASS><<<grid, TC_WARPS * 32, smem, st>>>(
-      M, N, nk, Ap, (long long)(pa / batch), Bp, (long long)(pb / batch), alpha, beta, Cin, ldcin,
-      sCin, C, ldc, sC, lower ? 1 : 0, tiles_m, tiles, items, stages, status, wait_limit);
+      M, N, nk, Ap, (long long)(pa / batch), Bp, (long long)((rot ? pa : pb) / batch), alpha,
+      beta, Cin, ldcin, sCin, C, ldc, sC, lower ? 1 : 0, tiles_m, tiles, items, stages, status,
+      wait_limit, rot ? nk / 2 : 0);
   return cudaGetLastError();
 }
 
@@ -573,7 +581,7 @@ cudaError_t tc_syr2k_lower(TcMode mode, int m, int k, const float* A, int lda, l
   const long long wl = wait_limit_of(wait_budget);
 #define TC_RUN(E, NP)                                                                           \
   run<E, NP>(m, m, 2 * k, a, b, -1.f, 1.f, A, lda, sA, Mout, ldm, sM, true, batch, ws, ws_bytes, \
-             status, wl, st)
+             status, wl, st, true)
   switch (mode) {
     case TcMode::TF32: return TC_RUN(float, 1);
     case TcMode::TF32x3: return TC_RUN(float, 3);
