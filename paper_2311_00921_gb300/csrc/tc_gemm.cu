@@ -411,7 +411,24 @@ tc_gemm_kernel(int M, int N, int nk, const unsigned char* __restrict__ Ap, long 
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[a]))
                          : "memory");
         }
-        if (row < M) {
+        // a chunk inside N and strictly below the diagonal (or a full matrix)
+        // needs no per-element test
+        const bool whole = n0 + c0 + 32 <= N && (!lower_only || tm > tn);
+        if (whole && row < M) {
+          float* cr = c + row + (long long)(n0 + c0) * ldc;
+          if (cin) {
+            const float* cir = cin + row + (long long)(n0 + c0) * ldcin;
+            float ci[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) ci[j] = cir[(long long)j * ldcin];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              cr[(long long)j * ldc] = fmaf(beta, ci[j], alpha * __uint_as_float(v[j]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cr[(long long)j * ldc] = alpha * __uint_as_float(v[j]);
+          }
+        } else if (row < M) {
           // C_in may be C itself: each element is read and written by this
           // thread only, so the 32 reads go out together before any write
           float ci[32];
