@@ -161,8 +161,8 @@ gemm_skinny_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int ld
 // register micro-tile each (rows lane + 32 p, columns warp + 4 q): with NQ = 4,
 // 16 FMAs per 8 shared-memory loads, as in the square tile, so the FP64 pipe
 // stays fed on the right-hand-side blocks of the solve and the residual matvec.
-// NQ = 2 serves blocks of at most 8 columns (a refinement lane's) without the
-// FMAs of 8 zero columns.
+// NQ = 2 serves blocks of at most 8 columns (a refinement lane's) and NQ = 1
+// blocks of at most 4, without the FMAs of zero columns.
 template <typename T, bool TA, bool TB, bool BETA, int NQ>
 __global__ void __launch_bounds__(128)
 gemm_n16_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, long long sA,
@@ -197,6 +197,7 @@ gemm_n16_kernel(int m, int n, int k, T alpha, const T* __restrict__ A, int lda, 
 #pragma unroll
     for (int e0 = 0; e0 < NB * TBK; e0 += TNT) {
       const int e = e0 + threadIdx.x;
+      if (NB * TBK % TNT != 0 && e >= NB * TBK) break;   // NQ = 1: half the threads load
       int j, kk;
       if (!TB) { kk = e % TBK; j = e / TBK; } else { j = e % NB; kk = e / NB; }
       const int gk = k0 + kk;
@@ -491,12 +492,15 @@ void launch_gemm(int m, int n, int k, T alpha, const T* A, int lda, long long sA
                                                                ldb, sB, beta, C, ldc, sC);
     return;
   }
-  if (n > 4 && n <= 16) {
+  if (n >= 1 && n <= 16) {
     dim3 g((m + 127) / 128, 1, batch);
 #define N16_RUN(B_, NQ_)                                                                     \
   gemm_n16_kernel<T, TA, TB, B_, NQ_><<<g, 128, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, \
                                                         beta, C, ldc, sC)
-    if (n <= 8) {
+    if (n <= 4) {   // every thread busy on 4 rows of one column (the skinny kernel would idle
+                    // the warps past n)
+      if (useb) N16_RUN(true, 1); else N16_RUN(false, 1);
+    } else if (n <= 8) {
       if (useb) N16_RUN(true, 2); else N16_RUN(false, 2);
     } else {
       if (useb) N16_RUN(true, 4); else N16_RUN(false, 4);
