@@ -661,7 +661,7 @@ def run_batch(args):
     out["loop_ms"] = timed(loop)
     lds_loop = np.array([o.logdet() for o in objs])
     ms = min(out["batch_ms"], out["batch_graph_ms"])
-    res = {"metric": "batched uneven HSS-ULV factor+solve, 256 matrices (FP64)",
+    res = {"metric": f"batched uneven HSS-ULV factor+solve, {args.batch} matrices (FP64)",
            "value": fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
