@@ -53,3 +53,37 @@ def test_create_rejects_bad_shapes_without_touching_the_device():
     bad = hss.Shape(512, 256, 300, 1)          # rank > leaf
     assert lib.hss_create(ctypes.byref(bad), buf, buf, buf, buf, 0, ctypes.byref(out)) == -1
     assert lib.hss_create(None, buf, buf, buf, buf, 0, ctypes.byref(out)) == -1
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled here."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src = (f'#include <stdio.h>\n#include "hss.h"\nint main(void) {{\n'
+           f'  printf("%zu\\n", sizeof({struct}));\n{body}  return 0;\n}}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe],
+                       check=True, capture_output=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+@pytest.mark.parametrize("struct,cls", [("hss_shape", "Shape"), ("hss_options", "Options"),
+                                        ("hss_tuning", "Tuning")])
+def test_binding_structs_match_the_header(struct, cls):
+    """Every struct the binding passes by pointer has the header's size and field
+    offsets (a mismatch would shift every later field silently)."""
+    from paper_2311_00921_gb300 import hss
+    py = getattr(hss, cls)
+    fields = [f[0] for f in py._fields_]
+    c = _c_layout(struct, fields)
+    assert c[0] == ctypes.sizeof(py), (struct, c[0], ctypes.sizeof(py))
+    for f, off in zip(fields, c[1:]):
+        assert off == getattr(py, f).offset, (struct, f, off, getattr(py, f).offset)
