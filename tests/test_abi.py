@@ -87,3 +87,54 @@ def test_binding_structs_match_the_header(struct, cls):
     assert c[0] == ctypes.sizeof(py), (struct, c[0], ctypes.sizeof(py))
     for f, off in zip(fields, c[1:]):
         assert off == getattr(py, f).offset, (struct, f, off, getattr(py, f).offset)
+
+
+def _lib():
+    from paper_2311_00921_gb300 import hss
+    if not os.path.exists(hss.LIB_PATH):
+        pytest.skip("library not built (run __graft_entry__.build())")
+    return hss, hss.load()
+
+
+def test_create_refuses_bad_shapes_before_any_device_call():
+    """Argument errors of hss_create come back as HSS_ERR_INVALID_ARG from the
+    host-side checks, before the library touches a device."""
+    hss, lib = _lib()
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    out = ctypes.c_void_p()
+
+    def create(n, leaf, rank, levels, sizes=None, E=p, on_device=0):
+        sh = hss.Shape(n, leaf, rank, levels, sizes)
+        return lib.hss_create(ctypes.byref(sh), p, p, E, p, on_device, ctypes.byref(out))
+
+    assert lib.hss_create(None, p, p, p, p, 0, ctypes.byref(out)) == -1
+    assert create(1025 * 4, 1025, 16, 2) == -1          # leaf above 1024
+    assert create(64 * 4, 64, 65, 2) == -1              # rank above leaf
+    assert create(512 * 4, 512, 257, 2) == -1           # rank above 256
+    assert create(64, 64, 16, 0) == -1                  # no level
+    assert create(64 << 25, 64, 16, 25) == -1           # too many levels
+    assert create(64 * 4 + 1, 64, 16, 2) == -1          # n is not leaf * 2^L
+    assert create(64 * 4, 64, 16, 2, E=None) == -1      # transfers missing
+    sizes = (ctypes.c_int32 * 4)(60, 64, 64, 70)        # a leaf order above leaf
+    assert create(258, 64, 16, 2, ctypes.cast(sizes, ctypes.POINTER(ctypes.c_int32))) == -1
+    sizes = (ctypes.c_int32 * 4)(60, 64, 64, 60)        # orders not summing to n
+    assert create(250, 64, 16, 2, ctypes.cast(sizes, ctypes.POINTER(ctypes.c_int32))) == -1
+    sizes = (ctypes.c_int32 * 4)(60, 64, 64, 60)        # uneven trees come from the host
+    assert create(248, 64, 16, 2, ctypes.cast(sizes, ctypes.POINTER(ctypes.c_int32)),
+                  on_device=1) == -1
+    assert out.value is None
+
+
+def test_null_handles_and_error_names():
+    hss, lib = _lib()
+    d = ctypes.c_double()
+    assert lib.hss_factorize(None, None, None) == -1
+    assert lib.hss_solve(None, None, None, 1, 1, None) == -1
+    assert lib.hss_matvec(None, None, None, 1, 1, None) == -1
+    assert lib.hss_logdet(None, ctypes.byref(d)) == -1
+    assert lib.hss_sync(None) == -1
+    assert lib.hss_trace(None, 1) == -1
+    lib.hss_destroy(None)                               # a no-op
+    names = [lib.hss_strerror(c) for c in range(0, -9, -1)]
+    assert all(names) and len(set(names)) == len(names), names
